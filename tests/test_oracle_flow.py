@@ -1,0 +1,146 @@
+"""Pins of the oracle's full step: the flux condition is exact every step
+(Section 3.2: the prescribed flux matches exactly since Eq. potential is not
+approximate), mass is conserved in a closed box, the square-duct flow matches
+the Poiseuille series of Section 3.1 with second-order convergence, the result
+does not depend on tau at fixed viscosity-scaled gradient, and symmetry."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from lbm_inputs import duct_mask, random_mask, uniform_field
+
+
+def _perturbed(mask, seed, amp=0.01):
+    r = uniform_field((19,) + mask.shape, seed)
+    return O.W[:, None, None, None] * (1.0 + amp * r)
+
+
+@pytest.mark.parametrize("model", ["mrt", "bgk"])
+def test_inlet_flux_exact_every_step(model):
+    m = random_mask(7, 6, 10, 0.3, 11)
+    Q = 0.004
+    o = O.D3Q19Oracle(m, 0.8, model=model, Q=Q)
+    o.set_distributions(_perturbed(m, 12))
+    A = int((m[0] == 0).sum())
+    # Q = sum_i (rho_in - K_i) cancels O(1) terms: exact up to ~A * eps rounding
+    tol = 8 * A * np.finfo(float).eps
+    for _ in range(15):
+        o.step()
+        assert abs(o.q_in - Q) <= tol
+        # j is conserved by collision, so the stored state carries the same flux
+        assert abs(o.face_flux(0) - Q) <= tol
+        rho, _, _, _ = o.fields()
+        np.testing.assert_allclose(rho[0][m[0] == 0], o.rho_in, rtol=0, atol=2e-15)
+        rho_l = rho[-1][m[-1] == 0]
+        np.testing.assert_allclose(rho_l, 1.0, atol=2e-15)
+
+
+def test_fixed_pressure_inlet_mode():
+    m = duct_mask(6, 6, 10)
+    o = O.D3Q19Oracle(m, 1.0, inlet="pressure", rho_in=1.01)
+    o.step(5)
+    rho, _, _, _ = o.fields()
+    np.testing.assert_allclose(rho[0][m[0] == 0], 1.01, atol=2e-15)
+
+
+def test_closed_box_mass_conservation():
+    m = random_mask(6, 6, 8, 0.25, 21)
+    m[0] = 1
+    m[-1] = 1
+    o = O.D3Q19Oracle(m, 0.7, inlet=None, outlet=None)
+    o.set_distributions(_perturbed(m, 22, 0.05))
+    m0 = math.fsum(o.f.ravel().tolist())
+    for _ in range(40):
+        o.step()
+    m1 = math.fsum(o.f.ravel().tolist())
+    assert abs(m1 - m0) <= 1e-13 * m0
+
+
+def test_open_face_without_condition_is_rejected():
+    m = duct_mask(6, 6, 8)
+    o = O.D3Q19Oracle(m, 1.0, inlet=None, outlet="pressure")
+    with pytest.raises(ValueError):
+        o.step()
+
+
+def test_series_satisfies_duct_problem():
+    """The Section 3.1 series (a = w) solves nu lap(u) = dp/dz with u = 0 on the
+    walls, and its flow rate equals the classical closed form for a square duct
+    Q = 4 w^4 G / (3 mu) [1 - 192/pi^5 sum_{k odd} tanh(k pi / 2) / k^5]."""
+    w, nu, g = 3.0, 0.2, -1e-3
+    h = 1e-3
+    for x, y in [(0.0, 0.0), (1.1, -0.7), (-2.2, 1.9)]:
+        lap = (O.duct_velocity(x + h, y, w, nu, g) + O.duct_velocity(x - h, y, w, nu, g)
+               + O.duct_velocity(x, y + h, w, nu, g) + O.duct_velocity(x, y - h, w, nu, g)
+               - 4 * O.duct_velocity(x, y, w, nu, g)) / h ** 2
+        # the truncated series' Laplacian is a k <= 200 Fourier sum of a
+        # constant (slow, ~1/k convergence): ~1% pointwise
+        assert abs(nu * lap - g) < 2e-2 * abs(g)
+    for x in (-w, w):
+        assert abs(O.duct_velocity(x, 0.3, w, nu, g)) < 1e-9
+        assert abs(O.duct_velocity(0.3, x, w, nu, g)) < 1e-6 * O.duct_velocity(0, 0, w, nu, g)
+    s = sum(math.tanh(k * math.pi / 2) / k ** 5 for k in range(1, 400, 2))
+    closed = 4 * w ** 4 / (3 * nu) * (1 - 192 / math.pi ** 5 * s)
+    assert abs(O.duct_flow_rate_per_gradient(w, nu) - closed) < 2e-5 * closed
+
+
+def _duct_run(n, nz, tau, steps, ubar=1e-3):
+    m = duct_mask(n, n, nz)
+    A = (n - 2) ** 2
+    o = O.D3Q19Oracle(m, tau, Q=ubar * A)
+    o.step(steps)
+    rho, ux, uy, uz = o.fields()
+    zs = np.arange(nz // 4, 3 * nz // 4)
+    rbar = np.array([rho[z][m[z] == 0].mean() for z in zs])
+    dpdz = O.CS2 * np.polyfit(zs, rbar, 1)[0]
+    c = np.arange(1, n - 1) - (n - 1) / 2.0
+    X, Y = np.meshgrid(c, c, indexing="xy")
+    nu = O.CS2 * (tau - 0.5)
+    th = O.duct_velocity(X, Y, (n - 2) / 2.0, nu, dpdz)
+    sim = uz[nz // 2, 1:n - 1, 1:n - 1]
+    err = math.sqrt(((sim - th) ** 2).sum() / (th ** 2).sum())
+    return o, sim, err, dpdz, ubar * A
+
+
+@pytest.fixture(scope="module")
+def duct16():
+    return _duct_run(16, 64, 1.0, 2000)
+
+
+def test_poiseuille_profile_duct16(duct16):
+    """16x16x64 duct, tau = 1, mean inlet velocity 1e-3, 2000 steps: the mid-plane
+    profile matches the series with the measured gradient (w = 7)."""
+    o, sim, err, dpdz, Q = duct16
+    assert err < 5e-3
+    assert abs(sim.sum() - Q) < 1e-3 * Q
+    assert abs(o.q_out - Q) < 1e-3 * Q
+    assert dpdz < 0
+
+
+def test_duct_symmetry(duct16):
+    _, sim, _, _, _ = duct16
+    np.testing.assert_allclose(sim, sim.T, atol=1e-12 * sim.max())
+    np.testing.assert_allclose(sim, sim[::-1], atol=1e-12 * sim.max())
+    np.testing.assert_allclose(sim, sim[:, ::-1], atol=1e-12 * sim.max())
+
+
+def test_poiseuille_second_order_convergence(duct16):
+    _, _, e7, _, _ = duct16
+    _, _, e4, _, _ = _duct_run(10, 24, 1.0, 1500)
+    ratio = e4 / e7
+    assert 2.4 < ratio < 4.2, (e4, e7)
+
+
+def test_gradient_scales_with_viscosity():
+    """Appendix A: nu = c_s^2 (tau - 1/2).  At the same flux the measured gradient
+    divided by nu is the same for every tau (the wall position of the paper's
+    rate choice does not move with tau)."""
+    vals = []
+    for tau in (0.7, 1.0, 1.5):
+        _, _, err, dpdz, _ = _duct_run(10, 24, tau, 1500)
+        vals.append(dpdz / (O.CS2 * (tau - 0.5)))
+        assert err < 1e-2
+    vals = np.array(vals)
+    assert np.ptp(vals) < 2e-3 * abs(vals.mean())
