@@ -1,0 +1,369 @@
+#!/usr/bin/env python3
+"""Throughput of the D3Q19 flux-boundary LBM step on GB300 (MLUPS).
+
+Workload: single-fluid D3Q19 on a seeded synthetic 256^3 sphere pack (radii
+U[6,12], voxel porosity 0.35, 6 pure-pore reservoir layers at each z end, pores
+not reachable from the inlet filled), tau = 0.7, MRT collision, flux inlet with
+mean velocity 1e-4 (Q = 1e-4 * A), fixed-density outlet, FP32 storage.  One
+step = the inlet reduction (Eq. potential) + the fused pull/closure/collide
+kernel over every pore node.  MLUPS counts pore nodes only.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|fp64|fp16dev|bf16dev]
+  python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores
+
+N > 1 (under torchrun) runs N independent replicas, one per GPU, with no
+data-path communication (weak scaling); value = all ranks' pore updates / the
+slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from lbm_inputs import sphere_pack  # noqa: E402
+
+METRIC = "MLUPS"
+PACK = dict(n=256, rmin=6.0, rmax=12.0, porosity=0.35, seed=2024, reservoir=6)
+TAU = 0.7
+UBAR = 1e-4
+BYTES_PER_VALUE = {"fp64": 8, "fp32": 4, "fp16dev": 2, "bf16dev": 2}
+FALLBACK_HBM_GBS = 6800.0
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "k_step_fp32_sphere256.md")
+
+
+# --------------------------------------------------------------- helpers ---
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload():
+    mask, info = sphere_pack(PACK["n"], PACK["rmin"], PACK["rmax"], PACK["porosity"], PACK["seed"],
+                             reservoir=PACK["reservoir"])
+    a_in = int((mask[0] == 0).sum())
+    return mask, info, a_in
+
+
+def kernel_sources_sha():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1806_10589_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode() + b"\0" + fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_hbm_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as fh:
+            d = json.load(fh)
+        for k in ("hbm_gbs", "hbm_copy_gbs", "hbm_GBs"):
+            if k in d and d[k]:
+                return float(d[k]), "measured"
+    except (OSError, ValueError):
+        pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def profiled_traffic(sha):
+    """dram bytes per launch of the step kernel from the committed ncu summary,
+    if it was taken on the current kernel sources (else None)."""
+    try:
+        txt = open(PROFILE_TRAFFIC).read()
+    except OSError:
+        return None
+    m_sha = re.search(r"kernel_sources_sha:\s*([0-9a-f]+)", txt)
+    m_b = re.search(r"dram_bytes_per_launch_full_size:\s*([0-9.eE+]+)", txt)
+    if not (m_sha and m_b) or m_sha.group(1) != sha:
+        return None
+    return float(m_b.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [r.split(",") for r in self.file.read().strip().splitlines() if r.strip()]
+        self.file.close()
+        os.unlink(self.file.name)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+ORACLE_CHILD = r"""
+import json, sys, time
+import numpy as np
+sys.path.insert(0, sys.argv[1])
+import oracle
+m = np.load(sys.argv[2])
+steps = int(sys.argv[3]); tau = float(sys.argv[4]); Q = float(sys.argv[5])
+o = oracle.D3Q19Oracle(m, tau, "mrt", Q=Q)
+o.step(1)  # warm-up (allocations)
+t = time.perf_counter()
+o.step(steps)
+dt = time.perf_counter() - t
+print(json.dumps({"seconds": dt, "n_pore": int((m == 0).sum()), "steps": steps}))
+"""
+
+
+def oracle_rate(mask, steps, tau=TAU, ubar=UBAR):
+    """Run the FP64 CPU oracle on `mask` in a single-threaded child process;
+    return (MLUPS, seconds, n_pore)."""
+    a_in = int((mask[0] == 0).sum())
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
+        env[k] = "1"
+    with tempfile.TemporaryDirectory() as td:
+        p = os.path.join(td, "mask.npy")
+        np.save(p, mask)
+        r = subprocess.run([sys.executable, "-c", ORACLE_CHILD, ROOT, p, str(steps), str(tau),
+                            repr(ubar * a_in)], capture_output=True, text=True, env=env)
+    if r.returncode != 0:
+        raise RuntimeError("oracle child failed: " + r.stderr[-2000:])
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return d["n_pore"] * d["steps"] / d["seconds"] / 1e6, d["seconds"], d["n_pore"]
+
+
+def crop_for_budget(mask, seconds_per_step, probe_mlups):
+    """A z-slab of the pack (inlet side, full x/y extent shrunk if needed) whose
+    oracle step takes about `seconds_per_step`."""
+    nz, ny, nx = mask.shape
+    phi = float((mask == 0).mean())
+    cells = max(seconds_per_step * probe_mlups * 1e6 / phi, 4 * 4 * 3)
+    if cells >= nx * ny * 3:
+        dz = int(min(nz, max(3, cells // (nx * ny))))
+        return mask[:dz].copy()
+    side = int(max(4, min(nx, (cells / 3) ** 0.5)))
+    sub = mask[:3, :side, :side].copy()
+    sub[0][sub[0] == 1] = 0  # keep inlet/outlet pores in a tiny sample
+    return sub
+
+
+# ------------------------------------------------------------- our path ---
+def run_ours(args, rank, world, local):
+    import torch
+
+    from paper_1806_10589_gb300 import Lattice, load_library
+
+    torch.cuda.set_device(local)
+    load_library()
+    dev_name = torch.cuda.get_device_name(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    mask, info, a_in = workload()
+    Q = UBAR * a_in
+    prec = args.precision
+    stream = torch.cuda.current_stream()
+    lat = Lattice(mask, TAU, "mrt", prec, stream=stream)
+    lat.set_flux_bc(Q)
+    meta = lat.info()
+    n = meta["n_pore"]
+    K, W = args.steps, args.warmup
+
+    # warm-up: builds and replays the captured graphs
+    lat.step(W)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    lat.step(K)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    mon = lat.monitors(raise_unstable=False)
+    q_in, rho_in = lat.get_flux(4)
+
+    # dominant kernel: CUDA events around every launch, on the launching stream
+    k_prof = max(3, min(K, 400))
+    ms_step_k, ms_inlet_k = lat.time_kernels(k_prof)
+    s = BYTES_PER_VALUE[prec]
+    unit_bytes = 2 * 19 * s
+    achieved = unit_bytes * n / (ms_step_k * 1e-3) / 1e9
+    peak, peak_kind = measured_hbm_peak()
+    sha = kernel_sources_sha()
+    traffic = profiled_traffic(sha) if prec == "fp32" else None
+    lat.close()
+
+    # end to end through the public API with host buffers
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    with Lattice(mask, TAU, "mrt", prec, stream=stream) as lat2:
+        lat2.set_flux_bc(Q)
+        lat2.step(K)
+        rho, ux, uy, uz = lat2.fields()
+    t1 = time.perf_counter()
+    nz, ny, nx = mask.shape
+    h2d = 4 * (nx + 2) * (ny + 2) * (nz + 2) + 4 * n + 64
+    d2h = 4 * 8 * nx * ny * nz
+    e2e_mlups = n * K / (t1 - t0) / 1e6
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        probe_mlups, _, _ = oracle_rate(mask[:16].copy(), 1)
+        sample = crop_for_budget(mask, 8.0, probe_mlups)
+        c_mlups, c_sec, c_n = oracle_rate(sample, 2)
+        cpu = {"value": round(c_mlups, 4), "unit": METRIC, "cores": 1, "kind": "oracle",
+               "sample": "FP64 numpy oracle, single thread, 2 steps on the inlet-side %dx%dx%d slab of "
+                         "the same pack (%d pore nodes, %.1f s)" % (sample.shape[2], sample.shape[1],
+                                                                      sample.shape[0], c_n, c_sec)}
+
+    value = world * n * K / (ms * 1e-3) / 1e6
+    line = {
+        "metric": METRIC, "value": round(value, 2), "unit": METRIC, "n_gpus": world, "steps": K,
+        "warmup": W, "ms_per_step": round(ms / K, 6), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32",
+                                                          "fp16dev": "f16", "bf16dev": "bf16"}[prec],
+        "data": "synthetic",
+        "config": {"workload": "D3Q19 MRT flux-BC LBM, 256^3 sphere pack (radii 6-12, porosity %.3f, "
+                               "6+6 reservoir layers), tau 0.7, u_mean 1e-4, %s storage" % (info["porosity"], prec),
+                   "n_pore": n, "a_in": meta["a_in"], "box": [nx, ny, nz], "precision": prec,
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "inputs larger than L2 (two f buffers of %.0f MB each)" % (19 * s * n / 1e6),
+                   "device": dev_name},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": traffic,
+                     "kernel": "k_step", "kernel_ms": round(ms_step_k, 5),
+                     "bytes_per_unit": unit_bytes, "units_per_launch": n,
+                     "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind
+                     if peak_kind == "measured" else "fallback 6.8 TB/s",
+                     "inlet_kernel_ms": round(ms_inlet_k, 5)},
+        "cpu_baseline": cpu,
+        "e2e": {"value": round(e2e_mlups, 2), "unit": METRIC, "h2d_bytes_per_step": h2d / K,
+                "d2h_bytes_per_step": d2h / K},
+        "gpu_launches": 2 * K,
+        "clocks": clk,
+        "check": {"q_in": q_in, "Q": Q, "rho_in": rho_in, "u_max": mon["u_max"], "status": mon["status"]},
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+# ------------------------------------------------------ reference (oracle) ---
+def run_reference(args, rank, world, local):
+    if rank != 0:
+        return
+    mask, info, a_in = workload()
+    K, W = args.steps, args.warmup
+    probe_mlups, _, _ = oracle_rate(mask[:16].copy(), 1)
+    per_step = max(0.02, min(8.0, 60.0 / max(1, K + W)))
+    sample = crop_for_budget(mask, per_step, probe_mlups)
+    if W:
+        oracle_rate(sample, W)
+    mlups, sec, n_s = oracle_rate(sample, K)
+    desc = ("FP64 numpy oracle, single thread; each step is one oracle step on the inlet-side "
+            "%dx%dx%d sample of the 256^3 pack (%d pore nodes)" % (sample.shape[2], sample.shape[1],
+                                                                   sample.shape[0], n_s))
+    line = {"impl": "reference", "metric": METRIC, "value": round(mlups, 4), "unit": METRIC,
+            "n_gpus": world, "steps": K, "warmup": W, "ms_per_step": round(1e3 * sec / K, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "D3Q19 MRT flux-BC LBM, 256^3 sphere pack (radii 6-12, porosity %.3f, "
+                                   "6+6 reservoir layers), tau 0.7, u_mean 1e-4" % info["porosity"],
+                       "sample": desc},
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": desc, "value": round(mlups, 4),
+                             "unit": METRIC},
+            "e2e": {"value": round(mlups, 4), "unit": METRIC, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10000)
+    ap.add_argument("--warmup", type=int, default=200)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=list(BYTES_PER_VALUE), default="fp32")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world, local)
+    else:
+        run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

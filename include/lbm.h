@@ -1,0 +1,156 @@
+/*
+ * lbm.h - C ABI of the GB300 D3Q19 lattice Boltzmann solver with the adaptive
+ * volumetric-flux boundary condition of McClure, Li, Sheppard and Miller,
+ * "An adaptive volumetric flux boundary condition for lattice Boltzmann
+ * methods" (arXiv:1806.10589).
+ *
+ * The library owns its device memory.  Every call returns an lbm_status and
+ * never aborts; after a CUDA failure the context is poisoned (every later call
+ * returns LBM_ECUDA) and lbm_last_error() says what failed.  A context is used
+ * by one host thread at a time; separate contexts are independent.
+ *
+ * Conventions shared by all calls:
+ *   - voxel arrays are laid out [z][y][x] with x fastest, nx*ny*nz entries;
+ *   - the flow axis is z; the inlet is the plane z = 0 (face LBM_FACE_ZMIN),
+ *     the outlet the plane z = nz-1 (face LBM_FACE_ZMAX); the four lateral faces
+ *     are no-flow walls (Section 2 allows periodic or no-flow; this library
+ *     implements no-flow);
+ *   - lattice units throughout: rho0 = 1, c_s^2 = 1/3, nu = (tau - 1/2)/3.
+ */
+#ifndef GB300_LBM_H
+#define GB300_LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx; /* opaque, created by lbm_create, freed by lbm_destroy */
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_EINVAL = -1,       /* bad argument (message in lbm_last_error) */
+    LBM_ENOMEM = -2,       /* device or host allocation failed */
+    LBM_ECUDA = -3,        /* CUDA runtime error; sticky for the context */
+    LBM_EUNSUPPORTED = -4, /* valid request this library does not implement */
+    LBM_EUNSTABLE = -5,    /* NaN or |u| > 0.1 found by lbm_get_monitors */
+    LBM_ETIMEOUT = -6      /* reserved for bounded device waits */
+} lbm_status;
+
+/* Collision operator.  LBM_MODEL_MRT is Appendix A's multiple-relaxation-time
+ * operator with s_e = s_eps = s_pi = s_nu = 1/tau and s_q = s_m =
+ * 8(2 - s_nu)/(8 - s_nu); because every D3Q19 moment is even or odd in xi and
+ * the rates split the same way, it is evaluated as the equivalent
+ * two-relaxation-time update (s+ = s_nu, s- = s_q). */
+enum { LBM_MODEL_BGK = 0, LBM_MODEL_MRT = 1 };
+
+/* Storage of the 19 distributions in device memory (arithmetic is FP64 for
+ * LBM_PREC_FP64 and FP32 otherwise).  The 16-bit formats store the scaled
+ * deviation (f_q / w_q - 1) * 2^10 from the rest-state weight w_q. */
+enum { LBM_PREC_FP64 = 0, LBM_PREC_FP32 = 1, LBM_PREC_FP16DEV = 2, LBM_PREC_BF16DEV = 3 };
+
+/* Faces.  Only z faces are open (the paper derives the z-inlet condition). */
+enum { LBM_FACE_ZMIN = 4, LBM_FACE_ZMAX = 5 };
+
+/* Create a solver.  Cites: Eq. (d3q19), Eq. (LBE), Appendix A.
+ *   mask       host, nx*ny*nz bytes [z][y][x]: 0 = pore, 1 = solid; copied, the
+ *              caller keeps ownership.  Any other byte value is LBM_EINVAL.
+ *   nx, ny     1..2047;  nz 3..1023.
+ *   tau        > 0.5, the relaxation time (nu = (tau - 1/2)/3).
+ *   model      LBM_MODEL_*;  precision LBM_PREC_*.
+ *   out        receives the new context.
+ * The planes z = 0 and z = nz-1 must each hold at least one pore node
+ * (LBM_EINVAL otherwise).  Cells are initialised at rest, f = f^eq(rho=1, u=0).
+ * Defaults: inlet flux Q = 0, outlet density rho_out = 1, default CUDA stream. */
+int lbm_create(const uint8_t* mask, int nx, int ny, int nz, double tau, int model,
+               int precision, lbm_ctx** out);
+
+/* Prescribe the volumetric flux Q (lattice units, lu^3/lt) through the inlet,
+ * Eq. (flux).  Every step the inlet density is then set from Eq. (potential),
+ * rho_in = (rho0 Q + sum over inlet pore nodes of the known sum of Eq. inlet)/A,
+ * A = number of inlet pore nodes, and imposed with the Hecht-Harting pressure
+ * closure of Appendix B, so that the sum of u_z over the inlet equals Q to
+ * rounding.  face must be LBM_FACE_ZMIN; LBM_FACE_ZMAX returns
+ * LBM_EUNSUPPORTED (Section 2: a flux condition at both ends is neither needed
+ * nor advantageous).  Takes effect at the next step. */
+int lbm_set_flux_bc(lbm_ctx* ctx, int face, double Q);
+
+/* Prescribe a fixed density (pressure p = rho/3, Eq. pressure) on a face with the
+ * Appendix B closure.  LBM_FACE_ZMAX sets the outlet density (default 1.0);
+ * LBM_FACE_ZMIN switches the inlet from the flux condition to this fixed
+ * density until lbm_set_flux_bc is called again.  rho must be > 0. */
+int lbm_set_pressure_bc(lbm_ctx* ctx, int face, double rho);
+
+/* Use this CUDA stream (a cudaStream_t passed as void*, e.g. a PyTorch stream
+ * handle) for all later device work of this context.  NULL = default stream. */
+int lbm_set_stream(lbm_ctx* ctx, void* cuda_stream);
+
+/* Advance n >= 0 time steps, asynchronously on the context's stream.  One step
+ * follows Section 2's order: pull streaming with halfway bounce-back at solid
+ * voxels, the inlet density reduction (Eq. potential), the pressure closures at
+ * inlet and outlet (Appendix B), then collision (Appendix A) at every pore node.
+ * Runs of 64 steps are replayed from captured CUDA graphs. */
+int lbm_step(lbm_ctx* ctx, int n);
+
+/* Measured flux through a face: Q = sum of u_z over the face's pore nodes of the
+ * current state, in FP64, and the density imposed on that face at the last step
+ * (rho_in from Eq. potential for the inlet, rho_out for the outlet).  Either
+ * pointer may be NULL.  Synchronises the context's stream. */
+int lbm_get_flux(lbm_ctx* ctx, int face, double* Q, double* rho_bc);
+
+/* FP64 monitors of the current state: total mass sum(rho) over pore nodes,
+ * inlet and outlet fluxes, and max |u|.  Returns LBM_EUNSTABLE when a value is
+ * NaN or max |u| > 0.1 (Section 3.2's stability rule of thumb), else LBM_OK.
+ * Any pointer may be NULL.  Synchronises. */
+int lbm_get_monitors(lbm_ctx* ctx, double* mass, double* q_in, double* q_out, double* u_max);
+
+/* Macroscopic fields rho = sum f (Eq. m0), u = sum f xi / rho0 (Eq. m357) of the
+ * current state into caller-owned HOST arrays of nx*ny*nz doubles each ([z][y][x]);
+ * solid voxels are written as 0.  Any pointer may be NULL.  Synchronises. */
+int lbm_get_fields(lbm_ctx* ctx, double* rho, double* ux, double* uy, double* uz);
+
+/* The same fields as FP32 into caller-owned DEVICE buffers: rho (nx*ny*nz floats)
+ * and u (3*nx*ny*nz floats, components ux, uy, uz as three consecutive
+ * [z][y][x] blocks).  Asynchronous on the context's stream. */
+int lbm_get_fields_device(lbm_ctx* ctx, float* rho, float* u);
+
+/* Reset every pore node to f^eq(rho, u) from caller-owned HOST arrays of nx*ny*nz
+ * doubles ([z][y][x]; solid entries ignored), e.g. for a warm start.  A NULL
+ * velocity component means 0; NULL rho means 1.  Synchronises. */
+int lbm_set_fields(lbm_ctx* ctx, const double* rho, const double* ux, const double* uy,
+                   const double* uz);
+
+/* Copy all 19 distributions of the current state to/from a caller-owned HOST
+ * array of 19*nx*ny*nz doubles laid out [q][z][y][x], q in the order of
+ * Eq. (d3q19) (7..18 as fixed by Appendix B).  get writes 0 at solid voxels; set
+ * ignores them and encodes into the storage precision.  Synchronises. */
+int lbm_get_distributions(lbm_ctx* ctx, double* f);
+int lbm_set_distributions(lbm_ctx* ctx, const double* f);
+
+/* Sizes: number of pore nodes, inlet pore nodes (A), outlet pore nodes, steps
+ * taken since creation or the last set_* call.  Any pointer may be NULL. */
+int lbm_get_info(const lbm_ctx* ctx, int64_t* n_pore, int64_t* a_in, int64_t* a_out,
+                 int64_t* steps);
+
+/* Profiling aid: run n >= 1 steps as individual kernel launches on the context's
+ * stream with CUDA events around each launch and return the mean device time
+ * in milliseconds of the collide-stream kernel and of the inlet reduction
+ * kernel (either pointer may be NULL).  Advances the state by n steps exactly
+ * like lbm_step(ctx, n).  Synchronises. */
+int lbm_time_kernels(lbm_ctx* ctx, int n, float* ms_step_kernel, float* ms_inlet_kernel);
+
+/* Free all device and host memory of the context.  NULL is accepted. */
+int lbm_destroy(lbm_ctx* ctx);
+
+/* Message of the last error on ctx (or of the last failed lbm_create when
+ * ctx is NULL).  The string is owned by the library and valid until the next
+ * call on the same context. */
+const char* lbm_last_error(const lbm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GB300_LBM_H */

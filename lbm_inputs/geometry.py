@@ -7,6 +7,10 @@ so seeded sphere packs stand in for it.
 """
 from __future__ import annotations
 
+import json
+import os
+import tempfile
+
 import numpy as np
 
 
@@ -72,7 +76,7 @@ def _place_spheres(rng, shape_zyx, rmin, rmax, target_fraction, max_tries):
 
 
 def sphere_pack(n: int | tuple, rmin: float, rmax: float, porosity: float, seed: int,
-                reservoir: int = 0, lam_max: float = 1.8, max_tries: int = 2000):
+                reservoir: int = 0, lam_max: float = 1.8, max_tries: int = 2000, cache: bool = True):
     """Seeded synthetic sphere pack with a prescribed voxel porosity.
 
     Centres come from random sequential addition of non-overlapping spheres with
@@ -83,12 +87,20 @@ def sphere_pack(n: int | tuple, rmin: float, rmax: float, porosity: float, seed:
     inside a scaled sphere.  `reservoir` pure-pore layers are cleared at each z
     end and pores not connected to the inlet are filled.
 
-    Returns (mask, info) with info = {porosity, lam, n_spheres, seed}.
+    Returns (mask, info) with info = {porosity, lam, n_spheres, seed}.  Results
+    are cached under the system temporary directory (keyed by every argument)
+    because large packs take tens of seconds to generate.
     """
     if isinstance(n, int):
         nx = ny = nz = n
     else:
         nx, ny, nz = n
+    key = "pack_%d_%d_%d_%g_%g_%g_%d_%d_%g_%d" % (nx, ny, nz, rmin, rmax, porosity, seed, reservoir,
+                                                  lam_max, max_tries)
+    path = os.path.join(tempfile.gettempdir(), "lbm_inputs_cache", key + ".npz")
+    if cache and os.path.exists(path):
+        with np.load(path, allow_pickle=False) as z:
+            return z["mask"].copy(), json.loads(str(z["info"]))
     rng = np.random.default_rng(seed)
     cs, rs = _place_spheres(rng, (nz, ny, nx), rmin, rmax, 0.40, max_tries)
     ratio = np.full((nz, ny, nx), np.inf, dtype=np.float32)
@@ -116,6 +128,14 @@ def sphere_pack(n: int | tuple, rmin: float, rmax: float, porosity: float, seed:
     body = mask[reservoir:nz - reservoir] if reservoir else mask
     info = {"porosity": float(1.0 - body.mean()), "lam": lam, "n_spheres": int(len(rs)),
             "seed": int(seed), "reservoir": int(reservoir)}
+    if cache:
+        try:
+            os.makedirs(os.path.dirname(path), exist_ok=True)
+            tmp = path + ".%d.tmp.npz" % os.getpid()
+            np.savez(tmp, mask=mask, info=json.dumps(info))
+            os.replace(tmp, path)
+        except OSError:
+            pass
     return mask, info
 
 

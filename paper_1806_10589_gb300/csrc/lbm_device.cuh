@@ -1,0 +1,204 @@
+// Device-side building blocks of the D3Q19 flux-boundary solver: the lattice,
+// the storage codecs, the pull gather, the boundary closures and the collision.
+//
+// State convention: the device holds the shifted distributions
+//     d_q = f_q - w_q
+// (the deviation from the rest-state weight).  Every formula of the method is
+// affine in f with weight sums that cancel, so it is evaluated on d with the
+// density replaced by drho = rho - 1 (see each function).  This keeps the
+// significant digits of the small deviations in every storage format.
+#pragma once
+
+#include <cstdint>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+namespace lbm {
+
+// ---------------------------------------------------------------- lattice ---
+// Eq. (d3q19): q = 0 rest; 1..6 = +-x, +-y, +-z; 7..18 diagonals in the order
+// for which the Appendix B momentum rows hold: 7 (1,1,0) 8 (-1,-1,0) 9 (1,-1,0)
+// 10 (-1,1,0) 11 (1,0,1) 12 (-1,0,-1) 13 (1,0,-1) 14 (-1,0,1) 15 (0,1,1)
+// 16 (0,-1,-1) 17 (0,1,-1) 18 (0,-1,1).  Opposites pair as (odd q, q+1).
+__host__ __device__ constexpr int cx(int q) {
+    return (q == 1 || q == 7 || q == 9 || q == 11 || q == 13) ? 1
+         : (q == 2 || q == 8 || q == 10 || q == 12 || q == 14) ? -1 : 0;
+}
+__host__ __device__ constexpr int cy(int q) {
+    return (q == 3 || q == 7 || q == 10 || q == 15 || q == 17) ? 1
+         : (q == 4 || q == 8 || q == 9 || q == 16 || q == 18) ? -1 : 0;
+}
+__host__ __device__ constexpr int cz(int q) {
+    return (q == 5 || q == 11 || q == 14 || q == 15 || q == 18) ? 1
+         : (q == 6 || q == 12 || q == 13 || q == 16 || q == 17) ? -1 : 0;
+}
+__host__ __device__ constexpr int opp(int q) { return q == 0 ? 0 : ((q & 1) ? q + 1 : q - 1); }
+// weights: 1/3 rest, 1/18 axes, 1/36 diagonals (c_s^2 = 1/3)
+__host__ __device__ constexpr double wq(int q) {
+    return q == 0 ? 1.0 / 3.0 : (q <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
+}
+
+// Padded voxel-id grid entries (see the host side): >= 0 pore index,
+// SOLID for a solid or lateral out-of-box voxel, ZOUT outside the box in z.
+constexpr int SOLID = -1;
+constexpr int ZOUT = -2;
+
+// ----------------------------------------------------------------- codecs ---
+// Storage of d_q.  FP64 / FP32 store d_q; the 16-bit formats store
+// (d_q / w_q) * 2^10 = (f_q / w_q - 1) * 2^10.
+constexpr float DEV_SCALE = 1024.0f;
+
+struct StoreF64 {
+    using T = double;
+    using M = double;
+    template <int Q> __device__ static M dec(T v) { return v; }
+    template <int Q> __device__ static T enc(M v) { return v; }
+};
+struct StoreF32 {
+    using T = float;
+    using M = float;
+    template <int Q> __device__ static M dec(T v) { return v; }
+    template <int Q> __device__ static T enc(M v) { return v; }
+};
+struct StoreF16 {
+    using T = __half;
+    using M = float;
+    template <int Q> __device__ static M dec(T v) {
+        return __half2float(v) * float(wq(Q) / 1024.0);
+    }
+    template <int Q> __device__ static T enc(M v) {
+        return __float2half_rn(v * float(1024.0 / wq(Q)));
+    }
+};
+struct StoreBF16 {
+    using T = __nv_bfloat16;
+    using M = float;
+    template <int Q> __device__ static M dec(T v) {
+        return __bfloat162float(v) * float(wq(Q) / 1024.0);
+    }
+    template <int Q> __device__ static T enc(M v) {
+        return __float2bfloat16_rn(v * float(1024.0 / wq(Q)));
+    }
+};
+
+// ------------------------------------------------------- boundary state ---
+// FP64 scalars of the boundary conditions, in device memory so that captured
+// graphs pick up new values.  All densities are stored as drho = rho - 1.
+struct BcState {
+    double Q;              // prescribed inlet flux (Eq. flux)
+    double drho_in_fixed;  // inlet density when the inlet is in pressure mode
+    double drho_out;       // outlet density
+    int inlet_mode;        // 0 = flux (Eq. potential), 1 = fixed pressure
+    int pad_;
+    double drho_in;        // inlet density used by the current step (output of the reduction)
+    double inv_a_in;       // 1 / A
+};
+
+// ------------------------------------------------------------ helpers ---
+template <int Q>
+__device__ __forceinline__ int64_t grid_off(int sy, int sz) {
+    // padded-grid offset of the pull source x - xi_q
+    return -((int64_t)cz(Q) * sz + (int64_t)cy(Q) * sy + cx(Q));
+}
+
+// Pull one direction: d~_q(i) = d_q(src) for a pore source, own d_opp(i) for a
+// solid (halfway bounce-back) or z-outside source (overwritten by the closure).
+template <class S, int Q>
+__device__ __forceinline__ typename S::M pull(const typename S::T* __restrict__ fin, int64_t ns,
+                                              const int* __restrict__ grid, int64_t p, int i,
+                                              int sy, int sz) {
+    if (Q == 0) return S::template dec<0>(fin[i]);
+    const int id = __ldg(grid + p + grid_off<Q>(sy, sz));
+    if (id >= 0) return S::template dec<Q>(fin[(int64_t)Q * ns + id]);
+    return S::template dec<Q>(fin[(int64_t)opp(Q) * ns + i]);
+}
+
+// Known-sum of Eq. (inlet) on shifted values: K' = K - 1 (the weights of the
+// listed distributions sum to exactly 1).
+template <class M>
+__device__ __forceinline__ M inlet_known(const M* d) {
+    return d[0] + d[1] + d[2] + d[3] + d[4] + d[7] + d[8] + d[9] + d[10] +
+           M(2) * (d[6] + d[12] + d[13] + d[16] + d[17]);
+}
+// Mirror for the outlet: sum over xi_z = 0 plus twice xi_z = +1, minus 1.
+template <class M>
+__device__ __forceinline__ M outlet_known(const M* d) {
+    return d[0] + d[1] + d[2] + d[3] + d[4] + d[7] + d[8] + d[9] + d[10] +
+           M(2) * (d[5] + d[11] + d[14] + d[15] + d[18]);
+}
+
+// Appendix B, Hecht-Harting closure at a z-inlet with u_x = u_y = 0:
+// f5 = f6 + u_z/3, f11 = f12 + u_z/6 - N_x, f14 = f13 + u_z/6 + N_x,
+// f15 = f16 + u_z/6 - N_y, f18 = f17 + u_z/6 + N_y (rho0 = 1); pairs share a
+// weight so the same relations hold for d.
+template <class M>
+__device__ __forceinline__ void close_inlet(M* d, M uz) {
+    const M nx = M(0.5) * (d[1] + d[7] + d[9] - d[2] - d[10] - d[8]);
+    const M ny = M(0.5) * (d[3] + d[7] + d[10] - d[4] - d[9] - d[8]);
+    const M u3 = uz * M(1.0 / 3.0), u6 = uz * M(1.0 / 6.0);
+    d[5] = d[6] + u3;
+    d[11] = d[12] + u6 - nx;
+    d[14] = d[13] + u6 + nx;
+    d[15] = d[16] + u6 - ny;
+    d[18] = d[17] + u6 + ny;
+}
+// The same relations solved for the xi_z = -1 members at a z-outlet.
+template <class M>
+__device__ __forceinline__ void close_outlet(M* d, M uz) {
+    const M nx = M(0.5) * (d[1] + d[7] + d[9] - d[2] - d[10] - d[8]);
+    const M ny = M(0.5) * (d[3] + d[7] + d[10] - d[4] - d[9] - d[8]);
+    const M u3 = uz * M(1.0 / 3.0), u6 = uz * M(1.0 / 6.0);
+    d[6] = d[5] - u3;
+    d[12] = d[11] - u6 + nx;
+    d[13] = d[14] - u6 - nx;
+    d[16] = d[15] - u6 + ny;
+    d[17] = d[18] - u6 - ny;
+}
+
+// Collision on shifted values.  Appendix A's MRT with the paper's rates equals
+// the two-relaxation-time update
+//   f'_q = f_q - s+ (f+_q - feq+_q) - s- (f-_q - feq-_q)
+// with f+- = (f_q +- f_opp)/2, s+ = 1/tau, s- = 8(2 - s+)/(8 - s+); BGK is
+// s+ = s- = 1/tau.  feq_q - w_q = w_q (drho + 3 xi.u + 9/2 (xi.u)^2 - 3/2 u.u)
+// with u = j (rho0 = 1).
+template <class M, int A>
+__device__ __forceinline__ void relax_pair(M* d, M drho, M ux, M uy, M uz, M uu15, M sp, M sm) {
+    constexpr int B = opp(A);
+    const M xu = M(cx(A)) * ux + M(cy(A)) * uy + M(cz(A)) * uz;
+    const M w = M(wq(A));
+    const M ep = w * (drho + M(4.5) * xu * xu - uu15);
+    const M em = w * M(3) * xu;
+    const M dp = sp * (M(0.5) * (d[A] + d[B]) - ep);
+    const M dm = sm * (M(0.5) * (d[A] - d[B]) - em);
+    d[A] = d[A] - dp - dm;
+    d[B] = d[B] - dp + dm;
+}
+
+template <class M>
+__device__ __forceinline__ void moments(const M* d, M& drho, M& jx, M& jy, M& jz) {
+    drho = ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])) +
+           ((d[8] + d[9]) + (d[10] + d[11])) + ((d[12] + d[13]) + (d[14] + d[15])) +
+           ((d[16] + d[17]) + d[18]);
+    jx = (d[1] - d[2]) + (d[7] - d[8]) + (d[9] - d[10]) + (d[11] - d[12]) + (d[13] - d[14]);
+    jy = (d[3] - d[4]) + (d[7] - d[8]) + (d[10] - d[9]) + (d[15] - d[16]) + (d[17] - d[18]);
+    jz = (d[5] - d[6]) + (d[11] - d[12]) + (d[14] - d[13]) + (d[15] - d[16]) + (d[18] - d[17]);
+}
+
+template <class M>
+__device__ __forceinline__ void collide(M* d, M sp, M sm) {
+    M drho, ux, uy, uz;
+    moments(d, drho, ux, uy, uz);
+    const M uu15 = M(1.5) * (ux * ux + uy * uy + uz * uz);
+    d[0] = d[0] - sp * (d[0] - M(wq(0)) * (drho - uu15));
+    relax_pair<M, 1>(d, drho, ux, uy, uz, uu15, sp, sm);
+    relax_pair<M, 3>(d, drho, ux, uy, uz, uu15, sp, sm);
+    relax_pair<M, 5>(d, drho, ux, uy, uz, uu15, sp, sm);
+    relax_pair<M, 7>(d, drho, ux, uy, uz, uu15, sp, sm);
+    relax_pair<M, 9>(d, drho, ux, uy, uz, uu15, sp, sm);
+    relax_pair<M, 11>(d, drho, ux, uy, uz, uu15, sp, sm);
+    relax_pair<M, 13>(d, drho, ux, uy, uz, uu15, sp, sm);
+    relax_pair<M, 15>(d, drho, ux, uy, uz, uu15, sp, sm);
+    relax_pair<M, 17>(d, drho, ux, uy, uz, uu15, sp, sm);
+}
+
+}  // namespace lbm

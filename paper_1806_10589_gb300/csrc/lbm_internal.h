@@ -1,0 +1,55 @@
+// Internal interface between the C-ABI layer (lbm_api.cu) and the kernels
+// (lbm_kernels.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace lbm {
+
+struct BcState;
+
+// Geometry of one lattice on the device.
+struct DevLattice {
+    int64_t n;          // pore nodes
+    int64_t ns;         // row stride of the distribution arrays (elements)
+    int64_t a_in;       // inlet pore nodes: pore indices [0, a_in)
+    int64_t a_out;      // outlet pore nodes: pore indices [n - a_out, n)
+    int nx, ny, nz;     // voxel box
+    int sy, sz;         // strides of the padded id grid: (nx+2), (nx+2)(ny+2)
+    const uint32_t* vox;  // [n] padded linear voxel index of each pore node
+    const int* grid;      // [(nz+2)(ny+2)(nx+2)] padded id grid
+};
+
+struct Relax {
+    double sp, sm;  // s+ and s- of the two-relaxation-time form
+};
+
+// Monitor outputs (device), reduced in fixed order.
+struct MonitorOut {
+    double drho_sum;  // sum of (rho - 1) over pore nodes
+    double q_in;      // sum of u_z over inlet pore nodes
+    double q_out;     // sum of u_z over outlet pore nodes
+    double umax2;     // max |u|^2
+    double nan_count; // number of pore nodes with a non-finite moment
+};
+
+// Launchers.  `prec` is the LBM_PREC_* code.  All are asynchronous on `st`.
+cudaError_t launch_inlet_reduce(int prec, const void* fin, const DevLattice& L, BcState* bc,
+                                double* partials, unsigned* counter, cudaStream_t st);
+cudaError_t launch_step(int prec, const void* fin, void* fout, const DevLattice& L, Relax r,
+                        const BcState* bc, cudaStream_t st);
+cudaError_t launch_monitors(int prec, const void* f, const DevLattice& L, double* partials,
+                            unsigned* counter, MonitorOut* out, cudaStream_t st);
+cudaError_t launch_export(int prec, const void* f, const DevLattice& L, void* rho, void* ux,
+                          void* uy, void* uz, int out_double, cudaStream_t st);
+cudaError_t launch_init_eq(int prec, void* f, const DevLattice& L, const double* rho,
+                           const double* ux, const double* uy, const double* uz, cudaStream_t st);
+cudaError_t launch_encode(int prec, void* f, const DevLattice& L, const double* d, cudaStream_t st);
+cudaError_t launch_decode(int prec, const void* f, const DevLattice& L, double* d, cudaStream_t st);
+
+int elem_size(int prec);
+int inlet_reduce_blocks(const DevLattice& L);
+int monitor_blocks(const DevLattice& L);
+
+}  // namespace lbm

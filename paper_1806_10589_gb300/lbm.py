@@ -1,0 +1,207 @@
+"""ctypes binding of libgb300lbm.so (include/lbm.h): argument marshalling only.
+
+Every computation runs in the CUDA library.  The module-level functions carry
+the C names and signatures; `Lattice` is a thin owner of one lbm_ctx that
+marshals numpy arrays.  Importing works without a GPU; the first call that
+needs the library raises if libgb300lbm.so has not been built.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgb300lbm.so")
+
+LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSUPPORTED, LBM_EUNSTABLE, LBM_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
+LBM_MODEL_BGK, LBM_MODEL_MRT = 0, 1
+LBM_PREC_FP64, LBM_PREC_FP32, LBM_PREC_FP16DEV, LBM_PREC_BF16DEV = 0, 1, 2, 3
+LBM_FACE_ZMIN, LBM_FACE_ZMAX = 4, 5
+PRECISIONS = {"fp64": LBM_PREC_FP64, "fp32": LBM_PREC_FP32, "fp16dev": LBM_PREC_FP16DEV,
+              "bf16dev": LBM_PREC_BF16DEV}
+MODELS = {"bgk": LBM_MODEL_BGK, "mrt": LBM_MODEL_MRT}
+STATUS_NAMES = {0: "LBM_OK", -1: "LBM_EINVAL", -2: "LBM_ENOMEM", -3: "LBM_ECUDA",
+                -4: "LBM_EUNSUPPORTED", -5: "LBM_EUNSTABLE", -6: "LBM_ETIMEOUT"}
+
+_P = C.c_void_p
+_DP = C.POINTER(C.c_double)
+_I64P = C.POINTER(C.c_int64)
+_FP = C.POINTER(C.c_float)
+
+# name -> (restype, argtypes), the exact list declared in include/lbm.h
+SIGNATURES = {
+    "lbm_create": (C.c_int, [C.POINTER(C.c_uint8), C.c_int, C.c_int, C.c_int, C.c_double, C.c_int,
+                             C.c_int, C.POINTER(_P)]),
+    "lbm_set_flux_bc": (C.c_int, [_P, C.c_int, C.c_double]),
+    "lbm_set_pressure_bc": (C.c_int, [_P, C.c_int, C.c_double]),
+    "lbm_set_stream": (C.c_int, [_P, _P]),
+    "lbm_step": (C.c_int, [_P, C.c_int]),
+    "lbm_get_flux": (C.c_int, [_P, C.c_int, _DP, _DP]),
+    "lbm_get_monitors": (C.c_int, [_P, _DP, _DP, _DP, _DP]),
+    "lbm_get_fields": (C.c_int, [_P, _DP, _DP, _DP, _DP]),
+    "lbm_get_fields_device": (C.c_int, [_P, _P, _P]),
+    "lbm_set_fields": (C.c_int, [_P, _DP, _DP, _DP, _DP]),
+    "lbm_get_distributions": (C.c_int, [_P, _DP]),
+    "lbm_set_distributions": (C.c_int, [_P, _DP]),
+    "lbm_get_info": (C.c_int, [_P, _I64P, _I64P, _I64P, _I64P]),
+    "lbm_time_kernels": (C.c_int, [_P, C.c_int, _FP, _FP]),
+    "lbm_destroy": (C.c_int, [_P]),
+    "lbm_last_error": (C.c_char_p, [_P]),
+}
+
+_lib = None
+
+
+class LBMError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libgb300lbm.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libgb300lbm.so not built (%s); run __graft_entry__.build()" % path)
+    lib = C.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(a, ctype):
+    return None if a is None else a.ctypes.data_as(C.POINTER(ctype))
+
+
+def _make_raw(name):
+    def raw(*args):
+        return getattr(load_library(), name)(*args)
+    raw.__name__ = name
+    raw.__doc__ = "Raw C call %s (see include/lbm.h)." % name
+    return raw
+
+
+for _n in SIGNATURES:
+    globals()[_n] = _make_raw(_n)
+
+
+class Lattice:
+    """One solver context.  mask: uint8 [nz][ny][nx], 1 = solid."""
+
+    def __init__(self, mask, tau, model="mrt", precision="fp64", stream=None):
+        lib = load_library()
+        mask = np.ascontiguousarray(mask, dtype=np.uint8)
+        if mask.ndim != 3:
+            raise ValueError("mask must be 3-D [z][y][x]")
+        self.nz, self.ny, self.nx = mask.shape
+        self.shape = mask.shape
+        self.mask = mask
+        h = _P()
+        st = lib.lbm_create(_ptr(mask, C.c_uint8), self.nx, self.ny, self.nz, float(tau),
+                            MODELS[model] if isinstance(model, str) else int(model),
+                            PRECISIONS[precision] if isinstance(precision, str) else int(precision),
+                            C.byref(h))
+        if st != LBM_OK:
+            raise LBMError(st, lib.lbm_last_error(None).decode())
+        self._h = h
+        self._lib = lib
+        if stream is not None:
+            self.set_stream(stream)
+
+    # -- plumbing
+    def _check(self, st):
+        if st != LBM_OK:
+            raise LBMError(st, self._lib.lbm_last_error(self._h).decode())
+        return st
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.lbm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- calls
+    def set_stream(self, stream):
+        """stream: a torch.cuda.Stream, an integer cudaStream_t handle, or None."""
+        h = getattr(stream, "cuda_stream", stream)
+        self._check(self._lib.lbm_set_stream(self._h, _P(h) if h else None))
+
+    def set_flux_bc(self, Q, face=LBM_FACE_ZMIN):
+        self._check(self._lib.lbm_set_flux_bc(self._h, face, float(Q)))
+
+    def set_pressure_bc(self, face, rho):
+        self._check(self._lib.lbm_set_pressure_bc(self._h, face, float(rho)))
+
+    def step(self, n=1):
+        self._check(self._lib.lbm_step(self._h, int(n)))
+
+    def get_flux(self, face=LBM_FACE_ZMIN):
+        q, r = C.c_double(), C.c_double()
+        self._check(self._lib.lbm_get_flux(self._h, face, C.byref(q), C.byref(r)))
+        return q.value, r.value
+
+    def monitors(self, raise_unstable=True):
+        v = [C.c_double() for _ in range(4)]
+        st = self._lib.lbm_get_monitors(self._h, *[C.byref(x) for x in v])
+        if st != LBM_OK and (raise_unstable or st != LBM_EUNSTABLE):
+            self._check(st)
+        out = dict(zip(("mass", "q_in", "q_out", "u_max"), (x.value for x in v)))
+        out["status"] = st
+        return out
+
+    def fields(self):
+        arrs = [np.empty(self.shape) for _ in range(4)]
+        self._check(self._lib.lbm_get_fields(self._h, *[_ptr(a, C.c_double) for a in arrs]))
+        return tuple(arrs)
+
+    def fields_device(self, rho, u):
+        """rho, u: torch float32 CUDA tensors of nx*ny*nz and 3*nx*ny*nz elements."""
+        self._check(self._lib.lbm_get_fields_device(self._h, _P(rho.data_ptr()), _P(u.data_ptr())))
+
+    def set_fields(self, rho=None, ux=None, uy=None, uz=None):
+        cv = [None if a is None else np.ascontiguousarray(a, dtype=np.float64).reshape(self.shape)
+              for a in (rho, ux, uy, uz)]
+        self._check(self._lib.lbm_set_fields(self._h, *[_ptr(a, C.c_double) for a in cv]))
+
+    def distributions(self):
+        f = np.empty((19,) + self.shape)
+        self._check(self._lib.lbm_get_distributions(self._h, _ptr(f, C.c_double)))
+        return f
+
+    def set_distributions(self, f):
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        if f.shape != (19,) + self.shape:
+            raise ValueError("f must have shape (19,) + mask.shape")
+        self._check(self._lib.lbm_set_distributions(self._h, _ptr(f, C.c_double)))
+
+    def info(self):
+        v = [C.c_int64() for _ in range(4)]
+        self._check(self._lib.lbm_get_info(self._h, *[C.byref(x) for x in v]))
+        return dict(zip(("n_pore", "a_in", "a_out", "steps"), (x.value for x in v)))
+
+    def time_kernels(self, n):
+        a, b = C.c_float(), C.c_float()
+        self._check(self._lib.lbm_time_kernels(self._h, int(n), C.byref(a), C.byref(b)))
+        return a.value, b.value

@@ -1,0 +1,103 @@
+"""Host-side checks of the C ABI (no GPU): the library builds, loads and exports
+every function include/lbm.h declares; the binding covers the same list; the
+argument validation of lbm_create rejects bad input before any device work;
+the library and its binding never import the oracle."""
+import ctypes as C
+import os
+import re
+import shutil
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "lbm.h")
+
+
+def header_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbm_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not shutil.which("nvcc") and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("nvcc not available")
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_1806_10589_gb300 as pkg
+
+    return pkg.load_library()
+
+
+def test_header_lists_the_boundary():
+    fns = header_functions()
+    for name in ("lbm_create", "lbm_set_flux_bc", "lbm_step", "lbm_get_flux", "lbm_get_fields",
+                 "lbm_destroy", "lbm_last_error"):
+        assert name in fns
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in header_functions():
+        assert hasattr(lib, name), name
+
+
+def test_binding_matches_header():
+    import paper_1806_10589_gb300 as pkg
+
+    assert sorted(pkg.SIGNATURES) == header_functions()
+
+
+def _create(lib, mask, nx, ny, nz, tau=1.0, model=1, prec=0):
+    h = C.c_void_p()
+    st = lib.lbm_create(mask.ctypes.data_as(C.POINTER(C.c_uint8)) if mask is not None else None,
+                        nx, ny, nz, tau, model, prec, C.byref(h))
+    return st, h
+
+
+def test_create_rejects_bad_arguments_before_device_work(lib):
+    m = np.zeros((6, 4, 4), np.uint8)
+    assert _create(lib, m, 4, 4, 2)[0] == -1          # nz < 3
+    assert _create(lib, m, 4, 4, 6, tau=0.5)[0] == -1  # tau <= 1/2
+    assert _create(lib, m, 4, 4, 6, model=7)[0] == -1
+    assert _create(lib, m, 4, 4, 6, prec=9)[0] == -1
+    assert _create(lib, None, 4, 4, 6)[0] == -1
+    bad = m.copy()
+    bad[2, 1, 1] = 2
+    assert _create(lib, bad, 4, 4, 6)[0] == -1
+    assert b"0 or 1" in lib.lbm_last_error(None)
+    closed = m.copy()
+    closed[0] = 1
+    assert _create(lib, closed, 4, 4, 6)[0] == -1
+    assert b"inlet" in lib.lbm_last_error(None)
+
+
+def test_null_context_calls_fail_cleanly(lib):
+    assert lib.lbm_step(None, 1) == -1
+    assert lib.lbm_set_flux_bc(None, 4, 1.0) == -1
+    assert lib.lbm_destroy(None) == 0
+
+
+def test_product_never_imports_the_oracle():
+    pkg = os.path.join(ROOT, "paper_1806_10589_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"^\s*(import|from)\s+oracle\b", txt, re.M), f
+                assert "oracle/" not in txt, f
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    from paper_1806_10589_gb300 import lbm
+
+    with pytest.raises(RuntimeError):
+        lbm.load_library.__wrapped__ if hasattr(lbm.load_library, "__wrapped__") else None
+        saved = lbm._lib
+        lbm._lib = None
+        try:
+            lbm.load_library(str(tmp_path / "nope.so"))
+        finally:
+            lbm._lib = saved

@@ -1,0 +1,216 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle on
+identical seeded inputs.
+
+Tolerances (written here, derived in the design notes):
+  * FP64 storage and arithmetic: max |f_gpu - f_oracle| <= 1e-11 * max |f|
+    (FMA contraction and tree-shaped sums only reorder rounding).
+  * FP32 (stores d = f - w, FP32 arithmetic): per step each value picks up a few
+    ulps of the largest deviation it is formed from, so after N steps
+    max |delta f| <= 20 * N * eps32 * max |d|  (d = f - w).
+  * FP16/BF16 deviation storage: every store rounds d/w * 2^10 to 11 (FP16) or 8
+    (BF16) significant bits; the bound is 4 * N * 2^-p * max |d|.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from lbm_inputs import duct_mask, random_mask, uniform_field, sphere_pack
+
+pytestmark = pytest.mark.gpu
+
+EPS32 = float(np.finfo(np.float32).eps)
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+    import __graft_entry__
+
+    __graft_entry__.build()
+    return torch
+
+
+def _lat(mask, tau, model, prec, torch):
+    from paper_1806_10589_gb300 import Lattice
+
+    return Lattice(mask, tau, model, prec, stream=torch.cuda.current_stream())
+
+
+def _f0(mask, seed, amp=0.01):
+    return O.W[:, None, None, None] * (1.0 + amp * uniform_field((19,) + mask.shape, seed))
+
+
+def _run_pair(mask, tau, model, prec, steps, torch, Q=0.002, seed=3, inlet="flux", rho_in=1.0,
+              rho_out=1.0, amp=0.01, chunks=None):
+    f0 = _f0(mask, seed, amp)
+    with _lat(mask, tau, model, prec, torch) as lat:
+        if inlet == "flux":
+            lat.set_flux_bc(Q)
+        else:
+            lat.set_pressure_bc(4, rho_in)
+        lat.set_pressure_bc(5, rho_out)
+        lat.set_distributions(f0)
+        for c in (chunks or [steps]):
+            lat.step(c)
+        got = lat.distributions()
+        flux = lat.get_flux(4)
+        fields = lat.fields()
+    ref = O.D3Q19Oracle(mask, tau, model, Q=Q, inlet=inlet, rho_in=rho_in, rho_out=rho_out)
+    ref.set_distributions(f0)
+    ref.step(steps)
+    return got, ref, flux, fields
+
+
+CASES = [  # (nx, ny, nz, p_solid, seed)
+    (4, 4, 6, 0.2, 0),
+    (5, 7, 9, 0.3, 1),
+    (8, 8, 12, 0.35, 2),
+    (13, 11, 10, 0.3, 3),
+]
+
+
+@pytest.mark.parametrize("case", CASES)
+@pytest.mark.parametrize("model", ["mrt", "bgk"])
+def test_fp64_random_masks(torch_cuda, case, model):
+    nx, ny, nz, p, seed = case
+    m = random_mask(nx, ny, nz, p, seed)
+    got, ref, (q_in, rho_in), _ = _run_pair(m, 0.8, model, "fp64", 25, torch_cuda, seed=seed + 50)
+    err = np.abs(got - ref.f).max() / np.abs(ref.f).max()
+    assert err <= 1e-11, err
+    assert abs(rho_in - ref.rho_in) <= 1e-12
+    A = int((m[0] == 0).sum())
+    assert abs(q_in - 0.002) <= 8 * A * np.finfo(float).eps
+
+
+def test_fp64_ragged_multi_tile(torch_cuda):
+    """~15k pore nodes: many 256-thread tiles, a ragged last tile and several
+    inlet-reduction blocks (A > 256)."""
+    m = random_mask(37, 29, 21, 0.3, 9)
+    got, ref, _, _ = _run_pair(m, 0.65, "mrt", "fp64", 12, torch_cuda, seed=91)
+    n = int((m == 0).sum())
+    assert n % 256 != 0 and int((m[0] == 0).sum()) > 256
+    assert np.abs(got - ref.f).max() / np.abs(ref.f).max() <= 1e-11
+
+
+def test_fp64_graph_path_matches_single_steps(torch_cuda):
+    """lbm_step(n >= 64) replays captured graphs; it must give the same bits as
+    the same number of single steps, and match the oracle."""
+    m = random_mask(6, 5, 8, 0.25, 4)
+    a, ref, _, _ = _run_pair(m, 0.9, "mrt", "fp64", 70, torch_cuda, chunks=[70])
+    b, _, _, _ = _run_pair(m, 0.9, "mrt", "fp64", 70, torch_cuda, chunks=[1] * 70)
+    c, _, _, _ = _run_pair(m, 0.9, "mrt", "fp64", 70, torch_cuda, chunks=[3, 64, 3])
+    np.testing.assert_array_equal(a, b)
+    np.testing.assert_array_equal(a, c)
+    assert np.abs(a - ref.f).max() / np.abs(ref.f).max() <= 1e-11
+
+
+def test_fp64_pressure_inlet(torch_cuda):
+    m = duct_mask(7, 6, 10)
+    got, ref, (_, rho_bc), _ = _run_pair(m, 1.0, "mrt", "fp64", 20, torch_cuda, inlet="pressure",
+                                         rho_in=1.004, rho_out=0.999)
+    assert np.abs(got - ref.f).max() / np.abs(ref.f).max() <= 1e-11
+    assert abs(rho_bc - 1.004) < 1e-15
+
+
+@pytest.fixture(scope="module")
+def duct16_pair(torch_cuda):
+    """The 16x16x64 duct, tau = 1, mean inlet velocity 1e-3 (Q = 0.196), 2000
+    steps from rest, FP64 (graph path)."""
+    m = duct_mask(16, 16, 64)
+    Q = 1e-3 * 196
+    with _lat(m, 1.0, "mrt", "fp64", torch_cuda) as lat:
+        lat.set_flux_bc(Q)
+        lat.step(2000)
+        got = lat.distributions()
+        fields = lat.fields()
+        mon = lat.monitors()
+        flux_in = lat.get_flux(4)
+        flux_out = lat.get_flux(5)
+    ref = O.D3Q19Oracle(m, 1.0, "mrt", Q=Q)
+    ref.step(2000)
+    return m, Q, got, fields, mon, flux_in, flux_out, ref
+
+
+def test_duct16_2000_steps_fp64(duct16_pair):
+    m, Q, got, fields, mon, (q_in, rho_in), (q_out, rho_out), ref = duct16_pair
+    assert np.abs(got - ref.f).max() / np.abs(ref.f).max() <= 1e-11
+    rho, ux, uy, uz = fields
+    r_rho, r_ux, r_uy, r_uz = ref.fields()
+    assert np.abs(uz - r_uz).max() <= 1e-11 * np.abs(r_uz).max()
+    assert np.abs(rho - r_rho).max() <= 1e-11
+    assert abs(q_in - Q) <= 1e-12
+    assert abs(rho_in - ref.rho_in) <= 1e-12
+    assert abs(q_out - ref.face_flux(63)) <= 1e-11 * Q
+    assert abs(rho_out - 1.0) == 0.0
+    assert abs(mon["mass"] - math.fsum(r_rho[m == 0].tolist())) <= 1e-10
+    assert mon["status"] == 0
+
+
+def test_fields_zero_at_solids(duct16_pair):
+    m, _, _, fields, _, _, _, _ = duct16_pair
+    for a in fields:
+        assert np.all(a[m == 1] == 0.0)
+
+
+def test_fp64_deterministic(torch_cuda):
+    m = random_mask(37, 29, 21, 0.3, 19)
+    a, _, _, _ = _run_pair(m, 0.7, "mrt", "fp64", 5, torch_cuda, seed=5)
+    b, _, _, _ = _run_pair(m, 0.7, "mrt", "fp64", 5, torch_cuda, seed=5)
+    np.testing.assert_array_equal(a, b)
+
+
+def test_set_fields_is_equilibrium(torch_cuda):
+    m = random_mask(9, 7, 8, 0.3, 8)
+    rng = np.random.default_rng(1)
+    rho = 1 + 0.01 * rng.standard_normal(m.shape)
+    u = 0.01 * rng.standard_normal((3,) + m.shape)
+    with _lat(m, 1.0, "mrt", "fp64", torch_cuda) as lat:
+        lat.set_fields(rho, *u)
+        got = lat.distributions()
+    want = O.equilibrium(rho, u[0], u[1], u[2])
+    want[:, m == 1] = 0
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("model", ["mrt", "bgk"])
+def test_fp32_parity(torch_cuda, model):
+    m = random_mask(13, 11, 10, 0.3, 3)
+    N = 25
+    got, ref, (q_in, _), _ = _run_pair(m, 0.8, model, "fp32", N, torch_cuda, seed=7)
+    d_ref = ref.f - O.W[:, None, None, None] * (m == 0)
+    err = np.abs(got - ref.f).max()
+    bound = 20 * N * EPS32 * np.abs(d_ref).max()
+    assert err <= bound, (err, bound)
+    A = int((m[0] == 0).sum())
+    assert abs(q_in - 0.002) <= 19 * A * EPS32 * np.abs(d_ref).max() * 4
+
+
+@pytest.mark.parametrize("prec,bits", [("fp16dev", 11), ("bf16dev", 8)])
+def test_16bit_deviation_storage_error(torch_cuda, prec, bits):
+    m = random_mask(13, 11, 10, 0.3, 3)
+    N = 10
+    got, ref, _, _ = _run_pair(m, 0.8, "mrt", prec, N, torch_cuda, seed=7)
+    d_ref = ref.f - O.W[:, None, None, None] * (m == 0)
+    err = np.abs(got - ref.f).max()
+    bound = 4 * N * 2.0 ** -bits * np.abs(d_ref).max()
+    assert np.isfinite(got).all()
+    assert err <= bound, (err, bound)
+
+
+def test_full_size_sphere_pack_fp32_one_step(torch_cuda):
+    """256^3 sphere pack (radii U[6,12], porosity 0.35, 6 reservoir layers), the
+    benchmark's FP32 configuration and launch shape, 2 steps from a seeded
+    perturbed state, all cells against the oracle."""
+    m, info = sphere_pack(256, 6, 12, 0.35, seed=2024, reservoir=6)
+    A = int((m[0] == 0).sum())
+    N = 2
+    got, ref, (q_in, _), _ = _run_pair(m, 0.7, "mrt", "fp32", N, torch_cuda, Q=1e-4 * A, seed=77,
+                                       amp=0.001)
+    d_ref = ref.f - O.W[:, None, None, None] * (m == 0)
+    err = np.abs(got - ref.f).max()
+    assert err <= 20 * N * EPS32 * np.abs(d_ref).max() + 4 * EPS32 * 1e-2, err
