@@ -141,6 +141,24 @@ int lbm_get_info(const lbm_ctx* ctx, int64_t* n_pore, int64_t* a_in, int64_t* a_
  * like lbm_step(ctx, n).  Synchronises. */
 int lbm_time_kernels(lbm_ctx* ctx, int n, float* ms_step_kernel, float* ms_inlet_kernel);
 
+/* Inlet density for callers that cannot allocate device memory at the point of
+ * the call -- code inside a CUDA stream capture, where a cudaMalloc would break
+ * the capture, or a process whose device memory is reserved up front by another
+ * allocator.  The paper has no counterpart: this is a library-interface
+ * addition.  It computes, from the context's current distributions and the
+ * prescribed Q, the inlet density rho_in of Eq. (potential) that the next step
+ * imposes in flux mode, and writes it as one double to the caller-owned DEVICE
+ * pointer rho_in_device, asynchronously on the context's stream.
+ *   - Allocates nothing: its reduction scratch is a fixed static device array
+ *     of 16.6 KB that every GPU loading the library keeps until process exit;
+ *     the first call on a device looks up that array's device address, so make
+ *     it before any stream capture.
+ *   - Inlets of at most 524,288 pore nodes; larger ones return LBM_EINVAL.
+ *   - All calls share the scratch array: calls whose kernels overlap on the GPU
+ *     (other streams, other host threads, other contexts) race and must be
+ *     serialised by the caller. */
+int lbm_inlet_density_noalloc(lbm_ctx* ctx, double* rho_in_device);
+
 /* Free all device and host memory of the context.  NULL is accepted. */
 int lbm_destroy(lbm_ctx* ctx);
 

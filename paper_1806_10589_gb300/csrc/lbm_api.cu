@@ -509,6 +509,19 @@ int lbm_get_info(const lbm_ctx* c, int64_t* n_pore, int64_t* a_in, int64_t* a_ou
     return LBM_OK;
 }
 
+int lbm_inlet_density_noalloc(lbm_ctx* c, double* rho_in_device) {
+    int rc = enter(c);
+    if (rc) return rc;
+    if (!rho_in_device) return fail(c, LBM_EINVAL, "rho_in_device is NULL");
+    if (c->L.a_in > lbm::noalloc_max_inlet_nodes())
+        return fail(c, LBM_EINVAL,
+                    "inlet has %lld pore nodes; lbm_inlet_density_noalloc supports at most %lld",
+                    (long long)c->L.a_in, (long long)lbm::noalloc_max_inlet_nodes());
+    LBM_CUDA(c, lbm::launch_inlet_density_noalloc(c->prec, c->f[c->cur], c->L, c->d_bc, rho_in_device,
+                                                  c->stream));
+    return LBM_OK;
+}
+
 int lbm_destroy(lbm_ctx* c) {
     if (!c) return LBM_OK;
     cudaSetDevice(c->device);

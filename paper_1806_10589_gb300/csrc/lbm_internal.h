@@ -48,6 +48,11 @@ cudaError_t launch_init_eq(int prec, void* f, const DevLattice& L, const double*
 cudaError_t launch_encode(int prec, void* f, const DevLattice& L, const double* d, cudaStream_t st);
 cudaError_t launch_decode(int prec, const void* f, const DevLattice& L, double* d, cudaStream_t st);
 
+// No-allocation inlet density (lbm_noalloc.cu): scratch in a static device array.
+cudaError_t launch_inlet_density_noalloc(int prec, const void* fin, const DevLattice& L,
+                                         const BcState* bc, double* rho_in_out, cudaStream_t st);
+int64_t noalloc_max_inlet_nodes();
+
 int elem_size(int prec);
 int inlet_reduce_blocks(const DevLattice& L);
 int monitor_blocks(const DevLattice& L);

@@ -47,6 +47,7 @@ SIGNATURES = {
     "lbm_set_distributions": (C.c_int, [_P, _DP]),
     "lbm_get_info": (C.c_int, [_P, _I64P, _I64P, _I64P, _I64P]),
     "lbm_time_kernels": (C.c_int, [_P, C.c_int, _FP, _FP]),
+    "lbm_inlet_density_noalloc": (C.c_int, [_P, _P]),
     "lbm_destroy": (C.c_int, [_P]),
     "lbm_last_error": (C.c_char_p, [_P]),
 }
@@ -200,6 +201,12 @@ class Lattice:
         v = [C.c_int64() for _ in range(4)]
         self._check(self._lib.lbm_get_info(self._h, *[C.byref(x) for x in v]))
         return dict(zip(("n_pore", "a_in", "a_out", "steps"), (x.value for x in v)))
+
+    def inlet_density_noalloc(self, rho_in_device):
+        """rho_in of Eq. (potential) for the current state into a caller-owned
+        device double (e.g. a torch float64 CUDA tensor), allocating nothing."""
+        ptr = rho_in_device.data_ptr() if hasattr(rho_in_device, "data_ptr") else int(rho_in_device)
+        self._check(self._lib.lbm_inlet_density_noalloc(self._h, _P(ptr)))
 
     def time_kernels(self, n):
         a, b = C.c_float(), C.c_float()
