@@ -359,6 +359,25 @@ def run_reference(args, rank, world, local):
     print(json.dumps(line), flush=True)
 
 
+def run_profile_case(args):
+    """Small, fixed launch sequence for ncu: create the benchmark lattice, W
+    single-step warm-up launches, then `steps` steps with per-launch events."""
+    import torch
+
+    from paper_1806_10589_gb300 import Lattice
+
+    torch.cuda.set_device(0)
+    mask, info, a_in = workload()
+    with Lattice(mask, TAU, "mrt", args.precision, stream=torch.cuda.current_stream()) as lat:
+        lat.set_flux_bc(UBAR * a_in)
+        for _ in range(args.warmup):
+            lat.step(1)
+        ms_step, ms_in = lat.time_kernels(args.steps)
+        n = lat.info()["n_pore"]
+    print(json.dumps({"profile_case": args.precision, "n_pore": n, "k_step_ms": ms_step,
+                      "k_inlet_reduce_ms": ms_in}))
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -367,11 +386,15 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=list(BYTES_PER_VALUE), default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-case", action="store_true",
+                    help="run the short fixed launch sequence used for ncu captures")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     rank, world, local = dist_env()
-    if args.impl == "reference":
+    if args.profile_case:
+        run_profile_case(args)
+    elif args.impl == "reference":
         run_reference(args, rank, world, local)
     else:
         run_ours(args, rank, world, local)
