@@ -87,6 +87,13 @@ int lbm_set_pressure_bc(lbm_ctx* ctx, int face, double rho);
  * handle) for all later device work of this context.  NULL = default stream. */
 int lbm_set_stream(lbm_ctx* ctx, void* cuda_stream);
 
+/* Select the step-kernel variant (a tuning knob; every variant computes the
+ * same step): 0 = one thread per pore node; 1 = persistent kernel whose
+ * neighbour ids and pulled values are staged in shared memory by cp.async one
+ * 256-node tile ahead (the default); 2 = the same with 128-node tiles.
+ * Unknown variants return LBM_EINVAL.  Synchronises. */
+int lbm_set_kernel(lbm_ctx* ctx, int variant);
+
 /* Advance n >= 0 time steps, asynchronously on the context's stream.  One step
  * follows Section 2's order: pull streaming with halfway bounce-back at solid
  * voxels, the inlet density reduction (Eq. potential), the pressure closures at
@@ -105,6 +112,14 @@ int lbm_get_flux(lbm_ctx* ctx, int face, double* Q, double* rho_bc);
  * NaN or max |u| > 0.1 (Section 3.2's stability rule of thumb), else LBM_OK.
  * Any pointer may be NULL.  Synchronises. */
 int lbm_get_monitors(lbm_ctx* ctx, double* mass, double* q_in, double* q_out, double* u_max);
+
+/* Steady-state criterion of Section 3.1 (Eq. stopping_criterion):
+ *   residual = sum_x |u(x,t) - u(x,t')| / sum_x |u(x,t)|
+ * over pore nodes (|.| the Euclidean norm per node, FP64 sums), where t' is the
+ * state at the previous call; the paper uses a lag t - t' of 1000 steps and
+ * stops at residual <= 1e-6.  The first call only stores the snapshot (it
+ * allocates 24 bytes per pore node once) and returns +infinity.  Synchronises. */
+int lbm_steady_residual(lbm_ctx* ctx, double* residual);
 
 /* Macroscopic fields rho = sum f (Eq. m0), u = sum f xi / rho0 (Eq. m357) of the
  * current state into caller-owned HOST arrays of nx*ny*nz doubles each ([z][y][x]);

@@ -7,6 +7,6 @@ CUDA path.
 from .lbm_oracle import (  # noqa: F401
     XI, W, OPP, NQ, CS2, RHO0, D3Q19Oracle, equilibrium, moment_matrix, relaxation_rates,
     collide_mrt, collide_bgk, stream_pull, stream_pull_loops, inlet_known_sum,
-    outlet_known_sum, flux_density, hh_closure_inlet, hh_closure_outlet, moments,
+    outlet_known_sum, flux_density, hh_closure_inlet, hh_closure_outlet, moments, steady_residual,
 )
 from .poiseuille import duct_velocity, duct_flow_rate_per_gradient  # noqa: F401

@@ -233,6 +233,15 @@ def hh_closure_outlet(P, rho):
     return uz
 
 
+def steady_residual(u_now, u_prev, pore):
+    """Section 3.1, Eq. (stopping_criterion): sum_x |u(x,t) - u(x,t-lag)| / sum_x |u(x,t)|
+    over pore nodes, |.| the Euclidean norm of the velocity vector; u arrays are
+    (3, nz, ny, nx)."""
+    du = np.sqrt(((np.asarray(u_now) - np.asarray(u_prev)) ** 2).sum(axis=0))[pore]
+    un = np.sqrt((np.asarray(u_now) ** 2).sum(axis=0))[pore]
+    return math.fsum(du.tolist()) / math.fsum(un.tolist())
+
+
 class D3Q19Oracle:
     """Single-fluid D3Q19 LBM on a voxel mask, stepped as Section 2 orders it:
     stream, then (1) the inlet density from Eq. (potential), (2) the pressure

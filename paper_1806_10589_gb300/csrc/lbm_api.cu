@@ -13,6 +13,7 @@
 #include <cstdint>
 #include <new>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -24,6 +25,10 @@
 namespace {
 
 constexpr int kGraphSteps = 64;  // steps per captured graph (even: parity preserved)
+#ifndef LBM_DEFAULT_STEP_VARIANT
+#define LBM_DEFAULT_STEP_VARIANT 1
+#endif
+constexpr int kDefaultStepVariant = LBM_DEFAULT_STEP_VARIANT;
 thread_local std::string g_create_error;
 
 }  // namespace
@@ -34,6 +39,7 @@ struct lbm_ctx {
     int model = 1, prec = 1;
     double tau = 1.0;
     lbm::Relax relax{};
+    lbm::StepConfig step_cfg{0, 0};
     lbm::DevLattice L{};
     void* f[2] = {nullptr, nullptr};
     int cur = 0;
@@ -41,11 +47,13 @@ struct lbm_ctx {
     int* d_grid = nullptr;
     lbm::BcState h_bc{};
     lbm::BcState* d_bc = nullptr;
-    double* d_red_partials = nullptr;
-    unsigned* d_red_counter = nullptr;
+    double* d_red_partials = nullptr;   // inlet reductions (prime and fused), per-block partials
+    unsigned* d_red_counter = nullptr;  // ticket of the stand-alone inlet reduction
+    unsigned* d_step_counter = nullptr; // ticket of the reduction fused into the step
     double* d_mon_partials = nullptr;
     unsigned* d_mon_counter = nullptr;
     lbm::MonitorOut* d_mon = nullptr;
+    double* d_u_ref = nullptr;  // velocity snapshot of the steady-state criterion (allocated on first use)
     cudaStream_t stream = nullptr;
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -96,10 +104,17 @@ int push_bc(lbm_ctx* c) {
 }
 
 int one_step(lbm_ctx* c, cudaStream_t st) {
-    LBM_CUDA(c, lbm::launch_inlet_reduce(c->prec, c->f[c->cur], c->L, c->d_bc, c->d_red_partials,
-                                         c->d_red_counter, st));
-    LBM_CUDA(c, lbm::launch_step(c->prec, c->f[c->cur], c->f[c->cur ^ 1], c->L, c->relax, c->d_bc, st));
+    LBM_CUDA(c, lbm::launch_step_cfg(c->prec, c->step_cfg, c->f[c->cur], c->f[c->cur ^ 1], c->cur, c->L,
+                                     c->relax, c->d_bc, c->d_red_partials, c->d_step_counter, st));
     c->cur ^= 1;
+    return LBM_OK;
+}
+
+// Inlet density for the current buffer when the state or Q changed outside a
+// step (steps produce the next density themselves).
+int prime_inlet(lbm_ctx* c) {
+    LBM_CUDA(c, lbm::launch_inlet_reduce(c->prec, c->f[c->cur], c->cur, c->L, c->d_bc, c->d_red_partials,
+                                         c->d_red_counter, c->stream));
     return LBM_OK;
 }
 
@@ -141,9 +156,11 @@ void release(lbm_ctx* c) {
     cudaFree(c->d_bc);
     cudaFree(c->d_red_partials);
     cudaFree(c->d_red_counter);
+    cudaFree(c->d_step_counter);
     cudaFree(c->d_mon_partials);
     cudaFree(c->d_mon_counter);
     cudaFree(c->d_mon);
+    cudaFree(c->d_u_ref);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
 }
 
@@ -206,7 +223,7 @@ int lbm_create(const uint8_t* mask, int nx, int ny, int nz, double tau, int mode
     std::vector<uint32_t> vox;
     vox.reserve((size_t)(ncell / 2 + 16));
     c->pore_voxel.reserve((size_t)(ncell / 2 + 16));
-    int64_t a_in = 0, a_out = 0;
+    int64_t a_in = 0, a_out = 0, a_01 = 0;
     for (int64_t z = 0; z < nz; ++z)
         for (int64_t y = 0; y < ny; ++y)
             for (int64_t x = 0; x < nx; ++x) {
@@ -228,6 +245,7 @@ int lbm_create(const uint8_t* mask, int nx, int ny, int nz, double tau, int mode
                 vox.push_back((uint32_t)p);
                 c->pore_voxel.push_back(v);
                 if (z == 0) ++a_in;
+                if (z <= 1) ++a_01;
                 if (z == nz - 1) ++a_out;
             }
     if (a_in == 0 || a_out == 0) {
@@ -240,16 +258,20 @@ int lbm_create(const uint8_t* mask, int nx, int ny, int nz, double tau, int mode
     c->L.ns = (n + 127) / 128 * 128;
     c->L.a_in = a_in;
     c->L.a_out = a_out;
+    c->L.a_01 = a_01;
     c->L.nx = nx;
     c->L.ny = ny;
     c->L.nz = nz;
     c->L.sy = (int)px;
     c->L.sz = (int)(px * py);
+    for (int q = 0; q < 19; ++q)
+        c->L.goff[q] = -(lbm::cz(q) * c->L.sz + lbm::cy(q) * c->L.sy + lbm::cx(q));
 
     // ---- device memory
     int rc = LBM_OK;
     const size_t fbytes = (size_t)19 * (size_t)c->L.ns * (size_t)lbm::elem_size(precision);
-    const int nb_red = lbm::inlet_reduce_blocks(c->L);
+    // per-tile partials of the inlet reductions (tiles of >= 128 nodes)
+    const int nb_red = std::max(lbm::inlet_reduce_blocks(c->L), (int)((a_01 + 127) / 128));
     const int nb_mon = lbm::monitor_blocks(c->L);
     if ((rc = dev_alloc(c, &c->f[0], fbytes)) || (rc = dev_alloc(c, &c->f[1], fbytes)) ||
         (rc = dev_alloc(c, &c->d_vox, vox.size() * sizeof(uint32_t))) ||
@@ -257,6 +279,7 @@ int lbm_create(const uint8_t* mask, int nx, int ny, int nz, double tau, int mode
         (rc = dev_alloc(c, &c->d_bc, sizeof(lbm::BcState))) ||
         (rc = dev_alloc(c, &c->d_red_partials, (size_t)nb_red * sizeof(double))) ||
         (rc = dev_alloc(c, &c->d_red_counter, sizeof(unsigned))) ||
+        (rc = dev_alloc(c, &c->d_step_counter, sizeof(unsigned))) ||
         (rc = dev_alloc(c, &c->d_mon_partials, (size_t)5 * nb_mon * sizeof(double))) ||
         (rc = dev_alloc(c, &c->d_mon_counter, sizeof(unsigned))) ||
         (rc = dev_alloc(c, &c->d_mon, sizeof(lbm::MonitorOut)))) {
@@ -271,13 +294,17 @@ int lbm_create(const uint8_t* mask, int nx, int ny, int nz, double tau, int mode
     if (e == cudaSuccess) e = cudaMemcpy(c->d_vox, vox.data(), vox.size() * 4, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(c->d_grid, grid.data(), grid.size() * 4, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(c->d_red_counter, 0, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(c->d_step_counter, 0, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMemset(c->d_mon_counter, 0, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMemset(c->f[0], 0, fbytes);
     if (e == cudaSuccess) e = cudaMemset(c->f[1], 0, fbytes);
     c->h_bc = lbm::BcState{};
     if (e == cudaSuccess) e = cudaMemcpy(c->d_bc, &c->h_bc, sizeof(lbm::BcState), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = lbm::launch_init_eq(precision, c->f[0], c->L, nullptr, nullptr, nullptr, nullptr, 0);
+    if (e == cudaSuccess)
+        e = lbm::launch_inlet_reduce(precision, c->f[0], 0, c->L, c->d_bc, c->d_red_partials, c->d_red_counter, 0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = lbm::configure_step(precision, kDefaultStepVariant, c->L, &c->step_cfg);
     if (e != cudaSuccess) {
         fail(nullptr, LBM_ECUDA, "lbm_create device setup: %s", cudaGetErrorString(e));
         release(c);
@@ -297,7 +324,8 @@ int lbm_set_flux_bc(lbm_ctx* c, int face, double Q) {
     if (!(Q == Q) || Q > 1e30 || Q < -1e30) return fail(c, LBM_EINVAL, "Q must be finite");
     c->h_bc.Q = Q;
     c->h_bc.inlet_mode = 0;
-    return push_bc(c);
+    if ((rc = push_bc(c))) return rc;
+    return prime_inlet(c);
 }
 
 int lbm_set_pressure_bc(lbm_ctx* c, int face, double rho) {
@@ -312,13 +340,30 @@ int lbm_set_pressure_bc(lbm_ctx* c, int face, double rho) {
     } else {
         return fail(c, LBM_EINVAL, "unknown face %d", face);
     }
-    return push_bc(c);
+    if ((rc = push_bc(c))) return rc;
+    return prime_inlet(c);
 }
 
 int lbm_set_stream(lbm_ctx* c, void* s) {
     int rc = enter(c);
     if (rc) return rc;
     c->stream = (cudaStream_t)s;
+    return LBM_OK;
+}
+
+int lbm_set_kernel(lbm_ctx* c, int variant) {
+    int rc = enter(c);
+    if (rc) return rc;
+    if (variant < 0 || variant > 2) return fail(c, LBM_EINVAL, "unknown step kernel variant %d", variant);
+    lbm::StepConfig cfg{};
+    LBM_CUDA(c, lbm::configure_step(c->prec, variant, c->L, &cfg));
+    LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (auto& g : c->graph)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+    c->step_cfg = cfg;
     return LBM_OK;
 }
 
@@ -342,31 +387,26 @@ int lbm_time_kernels(lbm_ctx* c, int n, float* ms_step, float* ms_inlet) {
     int rc = enter(c);
     if (rc) return rc;
     if (n < 1) return fail(c, LBM_EINVAL, "n must be >= 1");
-    std::vector<cudaEvent_t> ev((size_t)3 * n, nullptr);
+    std::vector<cudaEvent_t> ev((size_t)2 * n, nullptr);
     for (auto& e : ev) LBM_CUDA(c, cudaEventCreate(&e));
     for (int k = 0; k < n; ++k) {
-        LBM_CUDA(c, cudaEventRecord(ev[3 * k], c->stream));
-        LBM_CUDA(c, lbm::launch_inlet_reduce(c->prec, c->f[c->cur], c->L, c->d_bc, c->d_red_partials,
-                                             c->d_red_counter, c->stream));
-        LBM_CUDA(c, cudaEventRecord(ev[3 * k + 1], c->stream));
-        LBM_CUDA(c, lbm::launch_step(c->prec, c->f[c->cur], c->f[c->cur ^ 1], c->L, c->relax, c->d_bc,
-                                     c->stream));
-        LBM_CUDA(c, cudaEventRecord(ev[3 * k + 2], c->stream));
+        LBM_CUDA(c, cudaEventRecord(ev[2 * k], c->stream));
+        LBM_CUDA(c, lbm::launch_step_cfg(c->prec, c->step_cfg, c->f[c->cur], c->f[c->cur ^ 1], c->cur, c->L,
+                                         c->relax, c->d_bc, c->d_red_partials, c->d_step_counter, c->stream));
+        LBM_CUDA(c, cudaEventRecord(ev[2 * k + 1], c->stream));
         c->cur ^= 1;
     }
     LBM_CUDA(c, cudaStreamSynchronize(c->stream));
-    double t_in = 0.0, t_st = 0.0;
+    double t_st = 0.0;
     for (int k = 0; k < n; ++k) {
-        float a = 0.f, b = 0.f;
-        LBM_CUDA(c, cudaEventElapsedTime(&a, ev[3 * k], ev[3 * k + 1]));
-        LBM_CUDA(c, cudaEventElapsedTime(&b, ev[3 * k + 1], ev[3 * k + 2]));
-        t_in += a;
+        float b = 0.f;
+        LBM_CUDA(c, cudaEventElapsedTime(&b, ev[2 * k], ev[2 * k + 1]));
         t_st += b;
     }
     for (auto& e : ev) cudaEventDestroy(e);
     c->steps += n;
     if (ms_step) *ms_step = (float)(t_st / n);
-    if (ms_inlet) *ms_inlet = (float)(t_in / n);
+    if (ms_inlet) *ms_inlet = 0.0f;  // the inlet reduction runs inside the step kernel
     return LBM_OK;
 }
 
@@ -385,6 +425,27 @@ int lbm_get_monitors(lbm_ctx* c, double* mass, double* q_in, double* q_out, doub
     return LBM_OK;
 }
 
+int lbm_steady_residual(lbm_ctx* c, double* residual) {
+    int rc = enter(c);
+    if (rc) return rc;
+    if (!residual) return fail(c, LBM_EINVAL, "residual is NULL");
+    const bool first = c->d_u_ref == nullptr;
+    if (first) {
+        if ((rc = dev_alloc(c, &c->d_u_ref, (size_t)3 * c->L.n * sizeof(double)))) return rc;
+        LBM_CUDA(c, cudaMemsetAsync(c->d_u_ref, 0, (size_t)3 * c->L.n * sizeof(double), c->stream));
+    }
+    LBM_CUDA(c, lbm::launch_velocity_change(c->prec, c->f[c->cur], c->L, c->d_u_ref, c->d_mon_partials,
+                                            c->d_mon_counter, c->d_mon, c->stream));
+    lbm::MonitorOut m{};
+    LBM_CUDA(c, cudaMemcpyAsync(&m, c->d_mon, sizeof m, cudaMemcpyDeviceToHost, c->stream));
+    LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (first)
+        *residual = HUGE_VAL;
+    else
+        *residual = m.q_in > 0.0 ? m.drho_sum / m.q_in : (m.drho_sum > 0.0 ? HUGE_VAL : 0.0);
+    return LBM_OK;
+}
+
 int lbm_get_flux(lbm_ctx* c, int face, double* Q, double* rho_bc) {
     int rc = enter(c);
     if (rc) return rc;
@@ -394,7 +455,10 @@ int lbm_get_flux(lbm_ctx* c, int face, double* Q, double* rho_bc) {
     lbm::BcState b{};
     LBM_CUDA(c, cudaMemcpy(&b, c->d_bc, sizeof b, cudaMemcpyDeviceToHost));
     if (Q) *Q = face == LBM_FACE_ZMIN ? m.q_in : m.q_out;
-    if (rho_bc) *rho_bc = 1.0 + (face == LBM_FACE_ZMIN ? b.drho_in : b.drho_out);
+    if (rho_bc)
+        *rho_bc = 1.0 + (face == LBM_FACE_ZMAX ? b.drho_out
+                         : b.inlet_mode        ? b.drho_in_fixed
+                                               : b.drho_in[c->cur ^ 1]);
     return LBM_OK;
 }
 
@@ -450,7 +514,7 @@ int lbm_set_fields(lbm_ctx* c, const double* rho, const double* ux, const double
     cudaFree(d);
     if (e != cudaSuccess) return fail(c, LBM_ECUDA, "lbm_set_fields: %s", cudaGetErrorString(e));
     c->steps = 0;
-    return LBM_OK;
+    return prime_inlet(c);
 }
 
 int lbm_get_distributions(lbm_ctx* c, double* f) {
@@ -497,7 +561,7 @@ int lbm_set_distributions(lbm_ctx* c, const double* f) {
     cudaFree(d);
     if (e != cudaSuccess) return fail(c, LBM_ECUDA, "lbm_set_distributions: %s", cudaGetErrorString(e));
     c->steps = 0;
-    return LBM_OK;
+    return prime_inlet(c);
 }
 
 int lbm_get_info(const lbm_ctx* c, int64_t* n_pore, int64_t* a_in, int64_t* a_out, int64_t* steps) {

@@ -84,15 +84,76 @@ struct StoreBF16 {
 // ------------------------------------------------------- boundary state ---
 // FP64 scalars of the boundary conditions, in device memory so that captured
 // graphs pick up new values.  All densities are stored as drho = rho - 1.
+// drho_in[c] is the inlet density (Eq. potential) for the step that reads
+// distribution buffer c; the step that reads buffer c produces drho_in[c ^ 1].
 struct BcState {
     double Q;              // prescribed inlet flux (Eq. flux)
     double drho_in_fixed;  // inlet density when the inlet is in pressure mode
     double drho_out;       // outlet density
     int inlet_mode;        // 0 = flux (Eq. potential), 1 = fixed pressure
     int pad_;
-    double drho_in;        // inlet density used by the current step (output of the reduction)
-    double inv_a_in;       // 1 / A
+    double drho_in[2];     // per buffer parity, see above
 };
+
+// ------------------------------------------------------- cache hints ---
+// L2 eviction-priority hints (PTX createpolicy / .L2::cache_hint): the streamed
+// distributions are marked evict-first, the small index structures (id grid,
+// voxel list) evict-last, so the latter stay in L2 from one step to the next.
+__device__ __forceinline__ uint64_t l2_policy_evict_first() {
+    uint64_t p;
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t l2_policy_evict_last() {
+    uint64_t p;
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ double ld_hint(const double* a, uint64_t pol) {
+    double v;
+    asm("ld.global.nc.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(a), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ float ld_hint(const float* a, uint64_t pol) {
+    float v;
+    asm("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(a), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ __half ld_hint(const __half* a, uint64_t pol) {
+    unsigned short v;
+    asm("ld.global.nc.L2::cache_hint.b16 %0, [%1], %2;" : "=h"(v) : "l"(a), "l"(pol));
+    return __ushort_as_half(v);
+}
+__device__ __forceinline__ __nv_bfloat16 ld_hint(const __nv_bfloat16* a, uint64_t pol) {
+    unsigned short v;
+    asm("ld.global.nc.L2::cache_hint.b16 %0, [%1], %2;" : "=h"(v) : "l"(a), "l"(pol));
+    return __ushort_as_bfloat16(v);
+}
+__device__ __forceinline__ int ld_hint(const int* a, uint64_t pol) {
+    int v;
+    asm("ld.global.nc.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(v) : "l"(a), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ unsigned ld_hint(const unsigned* a, uint64_t pol) {
+    unsigned v;
+    asm("ld.global.nc.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(a), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ void st_hint(double* a, double v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(a), "d"(v), "l"(pol) : "memory");
+}
+__device__ __forceinline__ void st_hint(float* a, float v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(a), "f"(v), "l"(pol) : "memory");
+}
+__device__ __forceinline__ void st_hint(__half* a, __half v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.b16 [%0], %1, %2;" ::"l"(a), "h"(__half_as_ushort(v)), "l"(pol)
+                 : "memory");
+}
+__device__ __forceinline__ void st_hint(__nv_bfloat16* a, __nv_bfloat16 v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.b16 [%0], %1, %2;" ::"l"(a), "h"(__bfloat16_as_ushort(v)),
+                 "l"(pol)
+                 : "memory");
+}
 
 // ------------------------------------------------------------ helpers ---
 template <int Q>

@@ -15,10 +15,12 @@ struct DevLattice {
     int64_t ns;         // row stride of the distribution arrays (elements)
     int64_t a_in;       // inlet pore nodes: pore indices [0, a_in)
     int64_t a_out;      // outlet pore nodes: pore indices [n - a_out, n)
+    int64_t a_01;       // pore nodes on the planes z = 0 and z = 1: indices [0, a_01)
     int nx, ny, nz;     // voxel box
     int sy, sz;         // strides of the padded id grid: (nx+2), (nx+2)(ny+2)
     const uint32_t* vox;  // [n] padded linear voxel index of each pore node
     const int* grid;      // [(nz+2)(ny+2)(nx+2)] padded id grid
+    int goff[19];         // padded-grid offset of the pull source x - xi_q, per q
 };
 
 struct Relax {
@@ -35,12 +37,29 @@ struct MonitorOut {
 };
 
 // Launchers.  `prec` is the LBM_PREC_* code.  All are asynchronous on `st`.
-cudaError_t launch_inlet_reduce(int prec, const void* fin, const DevLattice& L, BcState* bc,
+// Inlet density of Eq. (potential) for buffer `fin` (parity `slot`) by a pull
+// over the inlet plane; used whenever the state or Q changes outside a step.
+cudaError_t launch_inlet_reduce(int prec, const void* fin, int slot, const DevLattice& L, BcState* bc,
                                 double* partials, unsigned* counter, cudaStream_t st);
-cudaError_t launch_step(int prec, const void* fin, void* fout, const DevLattice& L, Relax r,
-                        const BcState* bc, cudaStream_t st);
+// One full step fin (parity `slot`) -> fout; also produces drho_in[slot ^ 1].
+cudaError_t launch_step(int prec, const void* fin, void* fout, int slot, const DevLattice& L, Relax r,
+                        BcState* bc, double* partials, unsigned* counter, cudaStream_t st);
+int step_reduce_blocks(const DevLattice& L);
+
+// Step-kernel variant: 0 = one thread per node (k_step); 1 / 2 = persistent
+// cp.async-pipelined kernel (k_step_async) with 256 / 128-node tiles.
+struct StepConfig {
+    int variant;
+    int grid;  // persistent grid size of the pipelined kernel
+};
+cudaError_t configure_step(int prec, int variant, const DevLattice& L, StepConfig* cfg);
+cudaError_t launch_step_cfg(int prec, const StepConfig& cfg, const void* fin, void* fout, int slot,
+                            const DevLattice& L, Relax r, BcState* bc, double* partials, unsigned* counter,
+                            cudaStream_t st);
 cudaError_t launch_monitors(int prec, const void* f, const DevLattice& L, double* partials,
                             unsigned* counter, MonitorOut* out, cudaStream_t st);
+cudaError_t launch_velocity_change(int prec, const void* f, const DevLattice& L, double* u_ref,
+                                   double* partials, unsigned* counter, MonitorOut* out, cudaStream_t st);
 cudaError_t launch_export(int prec, const void* f, const DevLattice& L, void* rho, void* ux,
                           void* uy, void* uz, int out_double, cudaStream_t st);
 cudaError_t launch_init_eq(int prec, void* f, const DevLattice& L, const double* rho,

@@ -1,13 +1,18 @@
 // CUDA kernels of the D3Q19 flux-boundary step (sm_103a).
 //
-//   k_inlet_reduce  Eq. (potential): inlet density from the pulled known sums of
-//                   all inlet pore nodes, FP64 warp-shuffle/block reduction and
-//                   a deterministic last-block finish.
 //   k_step          one full time step for every pore node: pull streaming with
 //                   halfway bounce-back (Eq. LBE), the Appendix B closures at the
-//                   inlet/outlet planes, collision (Appendix A) and the store.
+//                   inlet/outlet planes with the inlet density of Eq. (potential),
+//                   collision (Appendix A) and the store.  The same launch also
+//                   forms the NEXT step's inlet density: every stored value that
+//                   the next step pulls into an inlet node's known sum (Eq.
+//                   inlet) is added, in FP64, by the node that produces it, then
+//                   a deterministic last-block finish writes drho_in[slot ^ 1].
+//   k_inlet_reduce  the same density by a pull over the inlet plane, for states
+//                   set from outside a step (creation, set_*, a new Q).
 //   k_monitors      FP64 mass / flux / max|u| / NaN reductions of a state.
 //   k_export, k_init_eq, k_encode, k_decode   field and state conversions.
+#include <algorithm>
 #include <utility>
 
 #include "lbm_device.cuh"
@@ -19,6 +24,15 @@ namespace {
 
 constexpr int kBlock = 256;
 constexpr int kReduceBlock = 256;
+// Resident 256-thread blocks per SM the step kernel is compiled for (caps its
+// registers at 65536 / (256 * n)); FP64 arithmetic is left unconstrained.
+#ifndef LBM_STEP_MIN_BLOCKS
+#define LBM_STEP_MIN_BLOCKS 4
+#endif
+template <class S>
+constexpr int step_min_blocks() {
+    return sizeof(typename S::M) == 8 ? 1 : LBM_STEP_MIN_BLOCKS;
+}
 
 template <int... Qs, class F>
 __device__ __forceinline__ void for_q(std::integer_sequence<int, Qs...>, F&& f) {
@@ -32,6 +46,78 @@ __device__ __forceinline__ void pull_all(typename S::M* d, const typename S::T* 
     for_q(AllQ{}, [&](auto qc) {
         constexpr int Q = decltype(qc)::value;
         d[Q] = pull<S, Q>(fin, L.ns, L.grid, p, i, L.sy, L.sz);
+    });
+}
+
+// ---------------------------------------------------- step-kernel access ---
+// Per-direction row pointers of the two distribution buffers, passed as kernel
+// parameters: every gather address is one multiply-add with a constant-bank
+// operand, and no register is spent on 19 hoisted row bases.
+template <class T>
+struct StepPtrs {
+    const T* in[19];
+    T* out[19];
+};
+
+// LBM_L2_HINTS: 0 = no hints; 1 = index structures evict-last; 2 = also the
+// distribution streams evict-first.
+#ifndef LBM_L2_HINTS
+#define LBM_L2_HINTS 1
+#endif
+
+template <class T>
+__device__ __forceinline__ T ld_index(const T* a, uint64_t pol) {
+#if LBM_L2_HINTS >= 1
+    return ld_hint(a, pol);
+#else
+    (void)pol;
+    return __ldg(a);
+#endif
+}
+template <class T>
+__device__ __forceinline__ T ld_stream(const T* a, uint64_t pol) {
+#if LBM_L2_HINTS >= 2
+    return ld_hint(a, pol);
+#else
+    (void)pol;
+    return __ldg(a);
+#endif
+}
+template <class T>
+__device__ __forceinline__ void st_stream(T* a, T v, uint64_t pol) {
+#if LBM_L2_HINTS >= 2
+    st_hint(a, v, pol);
+#else
+    (void)pol;
+    *a = v;
+#endif
+}
+
+// Pull all 19 values of node i (padded voxel p): a pore source gives its own
+// value, a solid or outside source the node's opposite value (halfway
+// bounce-back; the z-outside ones are replaced by the closure).
+template <class S>
+__device__ __forceinline__ void pull_step(typename S::M* d, const StepPtrs<typename S::T>& P,
+                                          const DevLattice& L, int64_t p, int i, uint64_t pol_f,
+                                          uint64_t pol_idx) {
+    for_q(AllQ{}, [&](auto qc) {
+        constexpr int Q = decltype(qc)::value;
+        if constexpr (Q == 0) {
+            d[0] = S::template dec<0>(ld_stream(P.in[0] + i, pol_f));
+        } else {
+            const int id = ld_index(L.grid + p + L.goff[Q], pol_idx);
+            const typename S::T* a = id >= 0 ? P.in[Q] + id : P.in[opp(Q)] + i;
+            d[Q] = S::template dec<Q>(ld_stream(a, pol_f));
+        }
+    });
+}
+
+template <class S>
+__device__ __forceinline__ void store_step(const typename S::M* d, const StepPtrs<typename S::T>& P,
+                                           int i, uint64_t pol_f) {
+    for_q(AllQ{}, [&](auto qc) {
+        constexpr int Q = decltype(qc)::value;
+        st_stream(P.out[Q] + i, S::template enc<Q>(d[Q]), pol_f);
     });
 }
 
@@ -55,6 +141,50 @@ __device__ __forceinline__ double warp_max(double v) {
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
     return v;
 }
+// Warp sums in the storage's arithmetic type (FP32 for the FP32/16-bit
+// formats): FP64 arithmetic is scarce on GB300, so per-node values and the
+// first 32-way level stay in M and only the block level runs in FP64.
+template <class M>
+__device__ __forceinline__ M warp_sum_m(M v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+template <class M>
+__device__ __forceinline__ M warp_max_m(M v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = v > __shfl_down_sync(0xffffffffu, v, o) ? v : __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+template <int NT, class M>
+__device__ __forceinline__ double block_sum_m(M v, double* sh) {
+    v = warp_sum_m(v);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) sh[wid] = (double)v;
+    __syncthreads();
+    double r = 0.0;
+    if (wid == 0) {
+        r = lane < NT / 32 ? sh[lane] : 0.0;
+        r = warp_sum(r);
+    }
+    __syncthreads();
+    return r;  // valid in thread 0
+}
+template <int NT, class M>
+__device__ __forceinline__ double block_max_m(M v, double* sh) {
+    v = warp_max_m(v);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) sh[wid] = (double)v;
+    __syncthreads();
+    double r = 0.0;
+    if (wid == 0) {
+        r = lane < NT / 32 ? sh[lane] : 0.0;
+        r = warp_max(r);
+    }
+    __syncthreads();
+    return r;
+}
+
 // Fixed-shape block sum: the result depends only on the inputs, not on timing.
 template <int NT>
 __device__ __forceinline__ double block_sum(double v, double* sh) {
@@ -91,14 +221,10 @@ __device__ __forceinline__ double block_max(double v, double* sh) {
 // rho_in - 1 = (Q + S') / A  (Eq. potential with rho0 = 1, since K = 1 + K').
 template <class S>
 __global__ void __launch_bounds__(kReduceBlock)
-k_inlet_reduce(const typename S::T* __restrict__ fin, DevLattice L, BcState* bc,
+k_inlet_reduce(const typename S::T* __restrict__ fin, int slot, DevLattice L, BcState* bc,
                double* __restrict__ partials, unsigned* __restrict__ counter) {
     __shared__ double sh[32];
     __shared__ bool last;
-    if (bc->inlet_mode != 0) {  // fixed-pressure inlet: nothing to reduce
-        if (blockIdx.x == 0 && threadIdx.x == 0) bc->drho_in = bc->drho_in_fixed;
-        return;
-    }
     const int64_t i64 = (int64_t)blockIdx.x * kReduceBlock + threadIdx.x;
     double k = 0.0;
     if (i64 < L.a_in) {
@@ -128,34 +254,292 @@ k_inlet_reduce(const typename S::T* __restrict__ fin, DevLattice L, BcState* bc,
     for (int j = threadIdx.x; j < (int)gridDim.x; j += kReduceBlock) s += __ldcg(partials + j);
     s = block_sum<kReduceBlock>(s, sh);
     if (threadIdx.x == 0) {
-        bc->drho_in = (bc->Q + s) / (double)L.a_in;
+        bc->drho_in[slot] = (bc->Q + s) / (double)L.a_in;
         *counter = 0u;
     }
 }
 
 // ---------------------------------------------------------- the step ---
+// Contribution of pore node i (on plane z = 0 or z = 1) to the next step's
+// inlet known sum S' = sum over inlet nodes of K'.  A value stored in direction
+// p lands, at the next pull, on node i + xi_p (if that is a pore) or bounces
+// back to i as direction opp(p).  It enters S' when it lands on the plane z = 0
+// in a direction with xi_z = 0 (weight 1) or xi_z = -1 (weight 2):
+//   z = 0:  all xi_z = 0 values (they stay on the plane either way), plus twice
+//           each xi_z = +1 value whose destination on z = 1 is solid;
+//   z = 1:  twice each xi_z = -1 value whose destination on z = 0 is a pore.
+// Values are taken as the next step will decode them from storage.
 template <class S>
-__global__ void __launch_bounds__(kBlock)
-k_step(const typename S::T* __restrict__ fin, typename S::T* __restrict__ fout, DevLattice L,
-       typename S::M sp, typename S::M sm, const BcState* __restrict__ bc) {
-    using M = typename S::M;
-    const int64_t i64 = (int64_t)blockIdx.x * kBlock + threadIdx.x;
-    if (i64 >= L.n) return;
-    const int i = (int)i64;
-    const int64_t p = __ldg(L.vox + i);
-    M d[19];
-    pull_all<S>(d, fin, L, p, i);
+__device__ __forceinline__ double next_inlet_part(const typename S::M* d, const DevLattice& L,
+                                                  int64_t p, int i) {
+    double s = 0.0;
+    auto val = [&](auto qc) -> double {
+        constexpr int Q = decltype(qc)::value;
+        return (double)S::template dec<Q>(S::template enc<Q>(d[Q]));
+    };
+    auto dest_is_pore = [&](auto qc) -> bool {
+        constexpr int Q = decltype(qc)::value;  // destination i + xi_Q = pull source of opp(Q)
+        return __ldg(L.grid + p + L.goff[opp(Q)]) >= 0;
+    };
     if (i < L.a_in) {
-        // Section 2: after streaming, before collision.  u_z from Eq. (inlet)
-        // with the density of Eq. (potential); then the Appendix B closure.
-        const M uz = M(bc->drho_in) - inlet_known(d);
-        close_inlet(d, uz);
-    } else if (i64 >= L.n - L.a_out) {
-        const M uz = outlet_known(d) - M(bc->drho_out);
-        close_outlet(d, uz);
+        for_q(std::integer_sequence<int, 0, 1, 2, 3, 4, 7, 8, 9, 10>{},
+              [&](auto qc) { s += val(qc); });
+        for_q(std::integer_sequence<int, 5, 11, 14, 15, 18>{},
+              [&](auto qc) { if (!dest_is_pore(qc)) s += 2.0 * val(qc); });
+    } else {
+        for_q(std::integer_sequence<int, 6, 12, 13, 16, 17>{},
+              [&](auto qc) { if (dest_is_pore(qc)) s += 2.0 * val(qc); });
     }
-    collide(d, sp, sm);
-    store_all<S>(d, fout, L.ns, i);
+    return s;
+}
+
+template <class S>
+__global__ void __launch_bounds__(kBlock, step_min_blocks<S>())
+k_step(const StepPtrs<typename S::T> P, int slot, DevLattice L, typename S::M sp, typename S::M sm,
+       BcState* bc, double* __restrict__ partials, unsigned* __restrict__ counter) {
+    using M = typename S::M;
+    __shared__ double sh[32];
+    __shared__ bool last;
+    const int64_t i64 = (int64_t)blockIdx.x * kBlock + threadIdx.x;
+    const int i = (int)i64;
+    double part = 0.0;
+    if (i64 < L.n) {
+#if LBM_L2_HINTS >= 2
+        const uint64_t pol_f = l2_policy_evict_first();
+#else
+        const uint64_t pol_f = 0;
+#endif
+#if LBM_L2_HINTS >= 1
+        const uint64_t pol_idx = l2_policy_evict_last();
+#else
+        const uint64_t pol_idx = 0;
+#endif
+        const int64_t p = ld_index(L.vox + i, pol_idx);
+        M d[19];
+        pull_step<S>(d, P, L, p, i, pol_f, pol_idx);
+        if (i < L.a_in) {
+            // Section 2: after streaming, before collision.  u_z from Eq. (inlet)
+            // with the density of Eq. (potential); then the Appendix B closure.
+            const M drin = bc->inlet_mode ? M(bc->drho_in_fixed) : M(bc->drho_in[slot]);
+            close_inlet(d, drin - inlet_known(d));
+        } else if (i64 >= L.n - L.a_out) {
+            const M uz = outlet_known(d) - M(bc->drho_out);
+            close_outlet(d, uz);
+        }
+        collide(d, sp, sm);
+        store_step<S>(d, P, i, pol_f);
+        if (i64 < L.a_01) part = next_inlet_part<S>(d, L, p, i);
+    }
+    // blocks that hold plane z = 0 or z = 1 nodes (block-uniform branch)
+    if ((int64_t)blockIdx.x * kBlock < L.a_01) {
+        const unsigned nb = (unsigned)((L.a_01 + kBlock - 1) / kBlock);
+        const double b = block_sum<kBlock>(part, sh);
+        if (threadIdx.x == 0) {
+            partials[blockIdx.x] = b;
+            __threadfence();
+            last = atomicAdd(counter, 1u) == nb - 1;
+        }
+        __syncthreads();
+        if (last) {
+            __threadfence();
+            double s = 0.0;
+            for (unsigned j = threadIdx.x; j < nb; j += kBlock) s += __ldcg(partials + j);
+            s = block_sum<kBlock>(s, sh);
+            if (threadIdx.x == 0) {
+                bc->drho_in[slot ^ 1] = (bc->Q + s) / (double)L.a_in;
+                *counter = 0u;
+            }
+        }
+    }
+}
+
+// ------------------------------------------------ pipelined step kernel ---
+// The same step as k_step, restructured for memory-level parallelism: a
+// persistent grid walks 256-node tiles (tile t, t + G, t + 2G, ...), and every
+// gather goes through cp.async into shared memory one tile ahead of its use:
+//   A(t): the 18 neighbour ids of tile t        (id grid -> smem, L2 evict-last)
+//   B(t): the 19 pulled values of tile t         (distributions -> smem)
+// While tile t is collided, B(t + G) and A(t + 2G) are in flight, so the loads
+// outstanding per SM no longer cost registers.  Each thread only reads back the
+// shared-memory slots its own copies filled, so the pipeline needs no barrier.
+// 16-bit values are fetched as the aligned 4-byte pair that contains them.
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+template <int BYTES>
+__device__ __forceinline__ void cp_async(unsigned dst, const void* src) {
+    if constexpr (BYTES == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_hint4(unsigned dst, const void* src, uint64_t pol) {
+    asm volatile("cp.async.ca.shared.global.L2::cache_hint [%0], [%1], 4, 4, %2;" ::"r"(dst), "l"(src), "l"(pol)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+template <class S>
+struct AsyncSlot {
+    using T = typename S::T;
+    static constexpr int kBytes = sizeof(T) >= 4 ? (int)sizeof(T) : 4;  // bytes fetched per value
+};
+
+template <int NT>
+constexpr size_t async_smem_bytes(int slot_bytes) {
+    return (size_t)18 * NT * 4 + (size_t)2 * 19 * NT * slot_bytes;
+}
+
+// A(t): neighbour ids of this thread's node of tile t into ids[q-1][tid].
+template <int NT>
+__device__ __forceinline__ void issue_ids(int* ids, const DevLattice& L, uint32_t p, uint64_t pol) {
+    for_q(std::make_integer_sequence<int, 18>{}, [&](auto qc) {
+        constexpr int Q = decltype(qc)::value + 1;
+        cp_async_hint4(smem_u32(ids + (Q - 1) * NT + threadIdx.x), L.grid + (int64_t)p + L.goff[Q], pol);
+    });
+}
+
+// B(t): the 19 pulled values of node i into vals[q][tid]; returns the bit mask
+// of 16-bit values that sit in the upper half of their fetched 4-byte pair.
+template <class S, int NT>
+__device__ __forceinline__ unsigned issue_vals(unsigned char* vals, const int* ids,
+                                               const StepPtrs<typename S::T>& P, int i) {
+    using T = typename S::T;
+    constexpr int SB = AsyncSlot<S>::kBytes;
+    unsigned hi = 0;
+    for_q(AllQ{}, [&](auto qc) {
+        constexpr int Q = decltype(qc)::value;
+        const T* a;
+        if constexpr (Q == 0) {
+            a = P.in[0] + i;
+        } else {
+            const int id = ids[(Q - 1) * NT + threadIdx.x];
+            a = id >= 0 ? P.in[Q] + id : P.in[opp(Q)] + i;
+        }
+        const unsigned dst = smem_u32(vals + ((size_t)Q * NT + threadIdx.x) * SB);
+        if constexpr (sizeof(T) == 2) {
+            const uintptr_t u = reinterpret_cast<uintptr_t>(a);
+            hi |= (unsigned)((u >> 1) & 1u) << Q;
+            cp_async<4>(dst, reinterpret_cast<const void*>(u & ~(uintptr_t)3));
+        } else {
+            cp_async<SB>(dst, a);
+        }
+    });
+    return hi;
+}
+
+template <class S, int NT>
+__device__ __forceinline__ void read_vals(typename S::M* d, const unsigned char* vals, unsigned hi) {
+    using T = typename S::T;
+    constexpr int SB = AsyncSlot<S>::kBytes;
+    for_q(AllQ{}, [&](auto qc) {
+        constexpr int Q = decltype(qc)::value;
+        const unsigned char* slot = vals + ((size_t)Q * NT + threadIdx.x) * SB;
+        if constexpr (sizeof(T) == 2) {
+            const T* pair = reinterpret_cast<const T*>(slot);
+            d[Q] = S::template dec<Q>(pair[(hi >> Q) & 1u]);
+        } else {
+            d[Q] = S::template dec<Q>(*reinterpret_cast<const T*>(slot));
+        }
+    });
+}
+
+template <class S, int NT>
+__global__ void __launch_bounds__(NT)
+k_step_async(const StepPtrs<typename S::T> P, int slot, DevLattice L, typename S::M sp,
+             typename S::M sm, BcState* bc, double* __restrict__ partials,
+             unsigned* __restrict__ counter) {
+    using M = typename S::M;
+    constexpr int SB = AsyncSlot<S>::kBytes;
+    extern __shared__ __align__(16) unsigned char smem[];
+    int* ids = reinterpret_cast<int*>(smem);
+    unsigned char* vals0 = smem + (size_t)18 * NT * 4;
+    unsigned char* vals1 = vals0 + (size_t)19 * NT * SB;
+    __shared__ double sh[32];
+    __shared__ bool last;
+
+    const int64_t ntiles = (L.n + NT - 1) / NT;
+    const int64_t nt01 = (L.a_01 + NT - 1) / NT;
+    const int64_t G = gridDim.x;
+    const uint64_t pol_idx = l2_policy_evict_last();
+    auto node = [&](int64_t t) -> int64_t { return t * NT + threadIdx.x; };
+
+    int64_t t = blockIdx.x;
+    if (t >= ntiles) return;
+    // prologue: A(t); wait; B(t); A(t + G)
+    uint32_t p_cur = 0, p_next = 0, p_next2 = 0;
+    if (node(t) < L.n) p_cur = __ldg(L.vox + node(t));
+    if (t + G < ntiles && node(t + G) < L.n) p_next = __ldg(L.vox + node(t + G));
+    if (t + 2 * G < ntiles && node(t + 2 * G) < L.n) p_next2 = __ldg(L.vox + node(t + 2 * G));
+    if (node(t) < L.n) issue_ids<NT>(ids, L, p_cur, pol_idx);
+    cp_async_commit();
+    cp_async_wait_all();
+    unsigned hi_cur = 0, hi_next = 0;
+    if (node(t) < L.n) hi_cur = issue_vals<S, NT>(vals0, ids, P, (int)node(t));
+    cp_async_commit();
+    if (t + G < ntiles && node(t + G) < L.n) issue_ids<NT>(ids, L, p_next, pol_idx);
+    cp_async_commit();
+
+    for (int k = 0; t < ntiles; ++k, t += G) {
+        unsigned char* vcur = (k & 1) ? vals1 : vals0;
+        unsigned char* vnext = (k & 1) ? vals0 : vals1;
+        cp_async_wait_all();  // B(t) and A(t + G) have landed
+        const int64_t tn = t + G, tn2 = t + 2 * G;
+        if (tn < ntiles && node(tn) < L.n) hi_next = issue_vals<S, NT>(vnext, ids, P, (int)node(tn));
+        cp_async_commit();
+        if (tn2 < ntiles && node(tn2) < L.n) issue_ids<NT>(ids, L, p_next2, pol_idx);
+        cp_async_commit();
+        const int64_t tn3 = t + 3 * G;
+        const uint32_t p_after = (tn3 < ntiles && node(tn3) < L.n) ? __ldg(L.vox + node(tn3)) : 0u;
+
+        // ---- collide tile t (its values are in vcur)
+        const int64_t i64 = node(t);
+        double part = 0.0;
+        if (i64 < L.n) {
+            const int i = (int)i64;
+            M d[19];
+            read_vals<S, NT>(d, vcur, hi_cur);
+            if (i < L.a_in) {
+                const M drin = bc->inlet_mode ? M(bc->drho_in_fixed) : M(bc->drho_in[slot]);
+                close_inlet(d, drin - inlet_known(d));
+            } else if (i64 >= L.n - L.a_out) {
+                const M uz = outlet_known(d) - M(bc->drho_out);
+                close_outlet(d, uz);
+            }
+            collide(d, sp, sm);
+            for_q(AllQ{}, [&](auto qc) {
+                constexpr int Q = decltype(qc)::value;
+                P.out[Q][i] = S::template enc<Q>(d[Q]);
+            });
+            if (i64 < L.a_01) part = next_inlet_part<S>(d, L, p_cur, i);
+        }
+        if (t < nt01) {  // tile holds plane z = 0 / z = 1 nodes (block-uniform)
+            const double b = block_sum<NT>(part, sh);
+            if (threadIdx.x == 0) {
+                partials[t] = b;
+                __threadfence();
+                last = atomicAdd(counter, 1u) == (unsigned)nt01 - 1;
+            }
+            __syncthreads();
+            if (last) {
+                __threadfence();
+                double s = 0.0;
+                for (int64_t j = threadIdx.x; j < nt01; j += NT) s += __ldcg(partials + j);
+                s = block_sum<NT>(s, sh);
+                if (threadIdx.x == 0) {
+                    bc->drho_in[slot ^ 1] = (bc->Q + s) / (double)L.a_in;
+                    *counter = 0u;
+                }
+            }
+        }
+        hi_cur = hi_next;
+        p_cur = p_next;
+        p_next = p_next2;
+        p_next2 = p_after;
+    }
+    cp_async_wait_all();
 }
 
 // ---------------------------------------------------------- monitors ---
@@ -167,7 +551,7 @@ k_monitors(const typename S::T* __restrict__ f, DevLattice L, double* __restrict
     __shared__ double sh[32];
     __shared__ bool last;
     const int64_t i64 = (int64_t)blockIdx.x * kReduceBlock + threadIdx.x;
-    double v[5] = {0, 0, 0, 0, 0};
+    M v[5] = {M(0), M(0), M(0), M(0), M(0)};
     if (i64 < L.n) {
         const int i = (int)i64;
         M d[19];
@@ -177,21 +561,21 @@ k_monitors(const typename S::T* __restrict__ f, DevLattice L, double* __restrict
         });
         M drho, jx, jy, jz;
         moments(d, drho, jx, jy, jz);
-        const double u2 = (double)jx * jx + (double)jy * jy + (double)jz * jz;
-        const bool bad = !isfinite((double)drho) || !isfinite(u2);
-        v[0] = bad ? 0.0 : (double)drho;
-        if (i64 < L.a_in && !bad) v[1] = (double)jz;
-        if (i64 >= L.n - L.a_out && !bad) v[2] = (double)jz;
-        v[3] = bad ? 0.0 : u2;
-        v[4] = bad ? 1.0 : 0.0;
+        const M u2 = jx * jx + jy * jy + jz * jz;
+        const bool bad = !isfinite((double)drho) || !isfinite((double)u2);
+        v[0] = bad ? M(0) : drho;
+        if (i64 < L.a_in && !bad) v[1] = jz;
+        if (i64 >= L.n - L.a_out && !bad) v[2] = jz;
+        v[3] = bad ? M(0) : u2;
+        v[4] = bad ? M(1) : M(0);
     }
     const int nb = gridDim.x;
     double r[5];
-    r[0] = block_sum<kReduceBlock>(v[0], sh);
-    r[1] = block_sum<kReduceBlock>(v[1], sh);
-    r[2] = block_sum<kReduceBlock>(v[2], sh);
-    r[3] = block_max<kReduceBlock>(v[3], sh);
-    r[4] = block_sum<kReduceBlock>(v[4], sh);
+    r[0] = block_sum_m<kReduceBlock>(v[0], sh);
+    r[1] = block_sum_m<kReduceBlock>(v[1], sh);
+    r[2] = block_sum_m<kReduceBlock>(v[2], sh);
+    r[3] = block_max_m<kReduceBlock>(v[3], sh);
+    r[4] = block_sum_m<kReduceBlock>(v[4], sh);
     if (threadIdx.x == 0) {
         for (int c = 0; c < 5; ++c) partials[(int64_t)c * nb + blockIdx.x] = r[c];
         __threadfence();
@@ -219,6 +603,63 @@ k_monitors(const typename S::T* __restrict__ f, DevLattice L, double* __restrict
         out->q_out = t2;
         out->umax2 = t3;
         out->nan_count = t4;
+        *counter = 0u;
+    }
+}
+
+// ------------------------------------------------- steady residual ---
+// Section 3.1 stopping criterion: sum_x |u(x,t) - u(x,t_ref)| and sum_x |u(x,t)|
+// (|.| the Euclidean norm per node), FP64; u_ref <- u(t) for the next call.
+template <class S>
+__global__ void __launch_bounds__(kReduceBlock)
+k_velocity_change(const typename S::T* __restrict__ f, DevLattice L, double* __restrict__ u_ref,
+                  double* __restrict__ partials, unsigned* __restrict__ counter, MonitorOut* out) {
+    using M = typename S::M;
+    __shared__ double sh[32];
+    __shared__ bool last;
+    const int64_t i64 = (int64_t)blockIdx.x * kReduceBlock + threadIdx.x;
+    M dn = M(0), un = M(0);
+    if (i64 < L.n) {
+        M d[19];
+        for_q(AllQ{}, [&](auto qc) {
+            constexpr int Q = decltype(qc)::value;
+            d[Q] = S::template dec<Q>(f[(int64_t)Q * L.ns + i64]);
+        });
+        M drho, jx, jy, jz;
+        moments(d, drho, jx, jy, jz);
+        const M u[3] = {jx, jy, jz};
+        M d2 = M(0), u2 = M(0);
+        for (int c = 0; c < 3; ++c) {
+            const M r = (M)u_ref[(int64_t)c * L.n + i64];
+            d2 += (u[c] - r) * (u[c] - r);
+            u2 += u[c] * u[c];
+            u_ref[(int64_t)c * L.n + i64] = (double)u[c];
+        }
+        dn = sqrt(d2);
+        un = sqrt(u2);
+    }
+    const int nb = gridDim.x;
+    const double b0 = block_sum_m<kReduceBlock>(dn, sh);
+    const double b1 = block_sum_m<kReduceBlock>(un, sh);
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = b0;
+        partials[(int64_t)nb + blockIdx.x] = b1;
+        __threadfence();
+        last = atomicAdd(counter, 1u) == (unsigned)nb - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double a0 = 0.0, a1 = 0.0;
+    for (int j = threadIdx.x; j < nb; j += kReduceBlock) {
+        a0 += __ldcg(partials + j);
+        a1 += __ldcg(partials + (int64_t)nb + j);
+    }
+    const double t0 = block_sum<kReduceBlock>(a0, sh);
+    const double t1 = block_sum<kReduceBlock>(a1, sh);
+    if (threadIdx.x == 0) {
+        out->drho_sum = t0;  // sum |u - u_ref|
+        out->q_in = t1;      // sum |u|
         *counter = 0u;
     }
 }
@@ -306,27 +747,66 @@ cudaError_t dispatch(int prec, F&& f) {
 
 int elem_size(int prec) { return prec == 0 ? 8 : prec == 1 ? 4 : 2; }
 int inlet_reduce_blocks(const DevLattice& L) { return (int)blocks_for(L.a_in, kReduceBlock); }
+int step_reduce_blocks(const DevLattice& L) { return (int)blocks_for(L.a_01, kBlock); }
 int monitor_blocks(const DevLattice& L) { return (int)blocks_for(L.n, kReduceBlock); }
 
-cudaError_t launch_inlet_reduce(int prec, const void* fin, const DevLattice& L, BcState* bc,
+cudaError_t launch_inlet_reduce(int prec, const void* fin, int slot, const DevLattice& L, BcState* bc,
                                 double* partials, unsigned* counter, cudaStream_t st) {
     return dispatch(prec, [&](auto s) {
         using S = decltype(s);
         k_inlet_reduce<S><<<inlet_reduce_blocks(L), kReduceBlock, 0, st>>>(
-            (const typename S::T*)fin, L, bc, partials, counter);
+            (const typename S::T*)fin, slot, L, bc, partials, counter);
         return cudaGetLastError();
     });
 }
 
-cudaError_t launch_step(int prec, const void* fin, void* fout, const DevLattice& L, Relax r,
-                        const BcState* bc, cudaStream_t st) {
+cudaError_t launch_step(int prec, const void* fin, void* fout, int slot, const DevLattice& L, Relax r,
+                        BcState* bc, double* partials, unsigned* counter, cudaStream_t st) {
     return dispatch(prec, [&](auto s) {
         using S = decltype(s);
         using M = typename S::M;
-        k_step<S><<<blocks_for(L.n, kBlock), kBlock, 0, st>>>(
-            (const typename S::T*)fin, (typename S::T*)fout, L, (M)r.sp, (M)r.sm, bc);
+        using T = typename S::T;
+        StepPtrs<T> P;
+        for (int q = 0; q < 19; ++q) {
+            P.in[q] = (const T*)fin + (int64_t)q * L.ns;
+            P.out[q] = (T*)fout + (int64_t)q * L.ns;
+        }
+        k_step<S><<<blocks_for(L.n, kBlock), kBlock, 0, st>>>(P, slot, L, (M)r.sp, (M)r.sm, bc, partials,
+                                                               counter);
         return cudaGetLastError();
     });
+}
+
+template <class S, int NT>
+cudaError_t launch_async_t(const void* fin, void* fout, int slot, const DevLattice& L, Relax r, BcState* bc,
+                           double* partials, unsigned* counter, cudaStream_t st, int grid) {
+    using T = typename S::T;
+    using M = typename S::M;
+    StepPtrs<T> P;
+    for (int q = 0; q < 19; ++q) {
+        P.in[q] = (const T*)fin + (int64_t)q * L.ns;
+        P.out[q] = (T*)fout + (int64_t)q * L.ns;
+    }
+    const size_t smem = async_smem_bytes<NT>(AsyncSlot<S>::kBytes);
+    k_step_async<S, NT><<<grid, NT, smem, st>>>(P, slot, L, (M)r.sp, (M)r.sm, bc, partials, counter);
+    return cudaGetLastError();
+}
+
+template <class S, int NT>
+cudaError_t config_async_t(int* grid, int64_t n) {
+    const size_t smem = async_smem_bytes<NT>(AsyncSlot<S>::kBytes);
+    cudaError_t e = cudaFuncSetAttribute(k_step_async<S, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0, dev = 0, sms = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_async<S, NT>, NT, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    const int64_t ntiles = (n + NT - 1) / NT;
+    *grid = (int)std::min<int64_t>((int64_t)per_sm * sms, ntiles);
+    return cudaSuccess;
 }
 
 cudaError_t launch_monitors(int prec, const void* f, const DevLattice& L, double* partials,
@@ -335,6 +815,16 @@ cudaError_t launch_monitors(int prec, const void* f, const DevLattice& L, double
         using S = decltype(s);
         k_monitors<S><<<monitor_blocks(L), kReduceBlock, 0, st>>>((const typename S::T*)f, L,
                                                                    partials, counter, out);
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t launch_velocity_change(int prec, const void* f, const DevLattice& L, double* u_ref,
+                                   double* partials, unsigned* counter, MonitorOut* out, cudaStream_t st) {
+    return dispatch(prec, [&](auto s) {
+        using S = decltype(s);
+        k_velocity_change<S><<<monitor_blocks(L), kReduceBlock, 0, st>>>((const typename S::T*)f, L, u_ref,
+                                                                         partials, counter, out);
         return cudaGetLastError();
     });
 }
@@ -375,6 +865,32 @@ cudaError_t launch_decode(int prec, const void* f, const DevLattice& L, double* 
         using S = decltype(s);
         k_decode<S><<<blocks_for(L.n, 256), 256, 0, st>>>((const typename S::T*)f, L, d);
         return cudaGetLastError();
+    });
+}
+
+cudaError_t configure_step(int prec, int variant, const DevLattice& L, StepConfig* cfg) {
+    cfg->variant = variant;
+    cfg->grid = 0;
+    if (variant == 0) return cudaSuccess;
+    return dispatch(prec, [&](auto s) {
+        using S = decltype(s);
+        if (variant == 1) return config_async_t<S, 256>(&cfg->grid, L.n);
+        if (variant == 2) return config_async_t<S, 128>(&cfg->grid, L.n);
+        return cudaErrorInvalidValue;
+    });
+}
+
+cudaError_t launch_step_cfg(int prec, const StepConfig& cfg, const void* fin, void* fout, int slot,
+                            const DevLattice& L, Relax r, BcState* bc, double* partials, unsigned* counter,
+                            cudaStream_t st) {
+    if (cfg.variant == 0) return launch_step(prec, fin, fout, slot, L, r, bc, partials, counter, st);
+    return dispatch(prec, [&](auto s) {
+        using S = decltype(s);
+        if (cfg.variant == 1)
+            return launch_async_t<S, 256>(fin, fout, slot, L, r, bc, partials, counter, st, cfg.grid);
+        if (cfg.variant == 2)
+            return launch_async_t<S, 128>(fin, fout, slot, L, r, bc, partials, counter, st, cfg.grid);
+        return cudaErrorInvalidValue;
     });
 }
 

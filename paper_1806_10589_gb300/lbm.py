@@ -13,7 +13,8 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libgb300lbm.so")
+# GB300_LBM_LIB selects another build of the same library (e.g. a tuning variant)
+LIB_PATH = os.environ.get("GB300_LBM_LIB") or os.path.join(_HERE, "libgb300lbm.so")
 
 LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSUPPORTED, LBM_EUNSTABLE, LBM_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
 LBM_MODEL_BGK, LBM_MODEL_MRT = 0, 1
@@ -37,9 +38,11 @@ SIGNATURES = {
     "lbm_set_flux_bc": (C.c_int, [_P, C.c_int, C.c_double]),
     "lbm_set_pressure_bc": (C.c_int, [_P, C.c_int, C.c_double]),
     "lbm_set_stream": (C.c_int, [_P, _P]),
+    "lbm_set_kernel": (C.c_int, [_P, C.c_int]),
     "lbm_step": (C.c_int, [_P, C.c_int]),
     "lbm_get_flux": (C.c_int, [_P, C.c_int, _DP, _DP]),
     "lbm_get_monitors": (C.c_int, [_P, _DP, _DP, _DP, _DP]),
+    "lbm_steady_residual": (C.c_int, [_P, _DP]),
     "lbm_get_fields": (C.c_int, [_P, _DP, _DP, _DP, _DP]),
     "lbm_get_fields_device": (C.c_int, [_P, _P, _P]),
     "lbm_set_fields": (C.c_int, [_P, _DP, _DP, _DP, _DP]),
@@ -155,6 +158,10 @@ class Lattice:
     def set_pressure_bc(self, face, rho):
         self._check(self._lib.lbm_set_pressure_bc(self._h, face, float(rho)))
 
+    def set_kernel(self, variant):
+        """Step-kernel variant: 0 per-node, 1 pipelined 256-node tiles, 2 pipelined 128."""
+        self._check(self._lib.lbm_set_kernel(self._h, int(variant)))
+
     def step(self, n=1):
         self._check(self._lib.lbm_step(self._h, int(n)))
 
@@ -171,6 +178,13 @@ class Lattice:
         out = dict(zip(("mass", "q_in", "q_out", "u_max"), (x.value for x in v)))
         out["status"] = st
         return out
+
+    def steady_residual(self):
+        """Section 3.1 criterion against the snapshot of the previous call
+        (+inf on the first call)."""
+        r = C.c_double()
+        self._check(self._lib.lbm_steady_residual(self._h, C.byref(r)))
+        return r.value
 
     def fields(self):
         arrs = [np.empty(self.shape) for _ in range(4)]

@@ -214,3 +214,102 @@ def test_full_size_sphere_pack_fp32_one_step(torch_cuda):
     d_ref = ref.f - O.W[:, None, None, None] * (m == 0)
     err = np.abs(got - ref.f).max()
     assert err <= 20 * N * EPS32 * np.abs(d_ref).max() + 4 * EPS32 * 1e-2, err
+
+
+def test_steady_residual_matches_oracle(torch_cuda):
+    """lbm_steady_residual against Eq. (stopping_criterion) of the oracle's fields
+    over the same lag, FP64."""
+    m = duct_mask(8, 7, 16)
+    Q = 0.01
+    with _lat(m, 0.9, "mrt", "fp64", torch_cuda) as lat:
+        lat.set_flux_bc(Q)
+        lat.step(40)
+        assert lat.steady_residual() == float("inf")
+        lat.step(25)
+        r_gpu = lat.steady_residual()
+    ref = O.D3Q19Oracle(m, 0.9, "mrt", Q=Q)
+    ref.step(40)
+    _, ux0, uy0, uz0 = ref.fields()
+    ref.step(25)
+    _, ux1, uy1, uz1 = ref.fields()
+    r_ref = O.steady_residual(np.stack([ux1, uy1, uz1]), np.stack([ux0, uy0, uz0]), m == 0)
+    assert abs(r_gpu - r_ref) <= 1e-11 * r_ref
+
+
+def test_convergence_harness_small_duct(torch_cuda):
+    """The time-to-steady harness on a small duct: the Section 3.1 rule converges,
+    and a second cold run reaches 0.1 % of its permeability."""
+    from paper_1806_10589_gb300 import convergence as cv
+
+    m = duct_mask(10, 10, 24)
+    Q = 1e-3 * 64
+    with _lat(m, 1.0, "mrt", "fp32", torch_cuda) as lat:
+        lat.set_flux_bc(Q)
+        ref = cv.run_to_residual(lat, Q, 1.0, lag=200, tol=1e-6, max_steps=20000)
+    assert ref["converged"] and abs(ref["q_out"] - Q) < 1e-4 * Q
+    with _lat(m, 1.0, "mrt", "fp32", torch_cuda) as lat:
+        lat.set_flux_bc(Q)
+        r = cv.run_to_reference(lat, Q, 1.0, ref["k"], check_every=20, max_steps=20000)
+    assert r["reached"] and r["steps"] < ref["steps"]
+
+
+def _run_variant(mask, tau, prec, steps, variant, torch, Q=0.002, seed=3, amp=0.01):
+    f0 = _f0(mask, seed, amp)
+    with _lat(mask, tau, "mrt", prec, torch) as lat:
+        lat.set_kernel(variant)
+        lat.set_flux_bc(Q)
+        lat.set_distributions(f0)
+        lat.step(steps)
+        got = lat.distributions()
+        q_in, rho_in = lat.get_flux(4)
+    return f0, got, q_in, rho_in
+
+
+@pytest.fixture(scope="module")
+def big_random_case():
+    """96x96x64 random pore space (~400k nodes: >1500 tiles of 256, so every
+    block of the persistent kernels walks several tiles), 70 steps in FP64 with
+    the oracle (exercises graphs, the pipelined prologue/steady state/tail)."""
+    m = random_mask(96, 96, 64, 0.3, 123)
+    f0 = _f0(m, 124)
+    ref = O.D3Q19Oracle(m, 0.75, "mrt", Q=0.05)
+    ref.set_distributions(f0)
+    ref.step(70)
+    return m, ref
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2])
+def test_step_variants_fp64_multi_tile(torch_cuda, big_random_case, variant):
+    m, ref = big_random_case
+    _, got, q_in, rho_in = _run_variant(m, 0.75, "fp64", 70, variant, torch_cuda, Q=0.05, seed=124)
+    assert np.abs(got - ref.f).max() / np.abs(ref.f).max() <= 1e-11
+    assert abs(rho_in - ref.rho_in) <= 1e-12
+    A = int((m[0] == 0).sum())
+    assert abs(q_in - 0.05) <= 8 * A * np.finfo(float).eps
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("prec,bound_bits", [("fp32", None), ("fp16dev", 11), ("bf16dev", 8)])
+def test_step_variants_reduced_precision(torch_cuda, variant, prec, bound_bits):
+    m = random_mask(37, 29, 21, 0.3, 9)
+    N = 10
+    f0, got, _, _ = _run_variant(m, 0.8, prec, N, variant, torch_cuda, seed=7)
+    ref = O.D3Q19Oracle(m, 0.8, "mrt", Q=0.002)
+    ref.set_distributions(f0)
+    ref.step(N)
+    d_ref = ref.f - O.W[:, None, None, None] * (m == 0)
+    err = np.abs(got - ref.f).max()
+    if bound_bits is None:
+        bound = 20 * N * EPS32 * np.abs(d_ref).max()
+    else:
+        bound = 4 * N * 2.0 ** -bound_bits * np.abs(d_ref).max()
+    assert err <= bound, (err, bound)
+
+
+def test_step_variants_agree_bitwise_on_interior(torch_cuda):
+    """Variants differ only in the order of the fused FP64 inlet sum, so after
+    one step from the same state every stored value agrees bit for bit."""
+    m = random_mask(37, 29, 21, 0.3, 10)
+    outs = [_run_variant(m, 0.8, "fp32", 1, v, torch_cuda, seed=11)[1] for v in (0, 1, 2)]
+    np.testing.assert_array_equal(outs[0], outs[1])
+    np.testing.assert_array_equal(outs[0], outs[2])

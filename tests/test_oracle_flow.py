@@ -144,3 +144,18 @@ def test_gradient_scales_with_viscosity():
         assert err < 1e-2
     vals = np.array(vals)
     assert np.ptp(vals) < 2e-3 * abs(vals.mean())
+
+
+def test_steady_residual_by_hand():
+    """Eq. (stopping_criterion) on a two-node example worked by hand:
+    |(3,4,0)-(0,0,0)| + |(0,0,1)-(0,0,2)| = 5 + 1 over |(3,4,0)| + |(0,0,1)| = 5 + 1."""
+    pore = np.array([[[True, True, False]]])
+    u_now = np.zeros((3, 1, 1, 3))
+    u_prev = np.zeros((3, 1, 1, 3))
+    u_now[:, 0, 0, 0] = (3, 4, 0)
+    u_now[:, 0, 0, 1] = (0, 0, 1)
+    u_prev[:, 0, 0, 1] = (0, 0, 2)
+    u_now[:, 0, 0, 2] = (9, 9, 9)  # solid: ignored
+    assert O.steady_residual(u_now, u_prev, pore) == 1.0
+    u_prev[:, 0, 0, 0] = (3, 4, 0)
+    assert abs(O.steady_residual(u_now, u_prev, pore) - 1.0 / 6.0) < 1e-16
