@@ -5,8 +5,11 @@ Workload: single-fluid D3Q19 on a seeded synthetic 256^3 sphere pack (radii
 U[6,12], voxel porosity 0.35, 6 pure-pore reservoir layers at each z end, pores
 not reachable from the inlet filled), tau = 0.7, MRT collision, flux inlet with
 mean velocity 1e-4 (Q = 1e-4 * A), fixed-density outlet, FP32 storage.  One
-step = the inlet reduction (Eq. potential) + the fused pull/closure/collide
-kernel over every pore node.  MLUPS counts pore nodes only.
+step = one launch of the step kernel over every pore node: pull streaming with
+bounce-back, the Appendix B closures with the inlet density of Eq. (potential),
+collision, store, and the FP64 reduction that forms the next step's inlet
+density.  MLUPS counts pore nodes only.  The default run also reports the
+time to steady flux (FP32 vs FP16/BF16 deviation storage, cold starts).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|fp64|fp16dev|bf16dev]
   python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores
@@ -218,6 +221,89 @@ def aggregate(n_local, K, ms_local, world, device=None):
     return total * K / (ms * 1e-3) / 1e6, ms
 
 
+def time_to_steady(mask, a_in, stream, max_steps=150000):
+    """Cold-start runs to steady flux on the benchmark workload: the FP32
+    reference k_inf by the Section 3.1 rule (residual over 1000 steps <= 1e-6),
+    then FP32 / FP16-dev / BF16-dev cold runs until k(t) is within 0.1 % of k_inf
+    and the outlet flux within 0.1 % of Q for 10 consecutive checks (every 100
+    steps).  Wall times include the checks."""
+    import torch
+
+    from paper_1806_10589_gb300 import Lattice, convergence as cv
+
+    Q = UBAR * a_in
+    out = {"criterion": "k within 0.1% of k_inf and Q_out within 0.1% of Q for 10 checks (every 100 steps); "
+                        "k_inf: FP32 cold run to sum|u(t)-u(t-1000)|/sum|u| <= 1e-6"}
+    with Lattice(mask, TAU, "mrt", "fp32", stream=stream) as lat:
+        lat.set_flux_bc(Q)
+        r = cv.run_to_residual(lat, Q, TAU, lag=1000, tol=1e-6, max_steps=max_steps,
+                               sync=torch.cuda.synchronize)
+    k_inf = r["k"]
+    out["k_inf"] = k_inf
+    out["k_inf_run"] = {"steps": r["steps"], "seconds": round(r["seconds"], 3), "residual": r["residual"],
+                        "converged": r["converged"], "q_out_rel_err": abs(r["q_out"] - Q) / Q}
+    for prec in ("fp32", "fp16dev", "bf16dev"):
+        with Lattice(mask, TAU, "mrt", prec, stream=stream) as lat:
+            lat.set_flux_bc(Q)
+            rr = cv.run_to_reference(lat, Q, TAU, k_inf, max_steps=min(max_steps, 60000),
+                                     sync=torch.cuda.synchronize)
+        out[prec] = {"steps": rr["steps"], "seconds": None if rr["seconds"] is None else round(rr["seconds"], 3),
+                     "reached": rr["reached"], "k_rel_err_at_end": (rr["k"] - k_inf) / k_inf,
+                     "q_out_rel_err_at_end": (rr["q_out"] - Q) / Q, "steps_run": rr["steps_run"]}
+    return out
+
+
+def ensemble_workload(n_members=64, seed=7):
+    """Config-4-shaped ensemble: cubes with edges drawn uniformly from 64..160,
+    each its own seeded sphere pack (radii U[6,12], porosity 0.35, no reservoirs),
+    flux targets u_mean U[5e-5, 2e-4] times the member's inlet pore count."""
+    rng = np.random.default_rng(seed)
+    edges = rng.integers(64, 161, size=n_members)
+    umean = rng.uniform(5e-5, 2e-4, size=n_members)
+    masks = []
+    for k, e in enumerate(edges):
+        m, _ = sphere_pack(int(e), 6.0, 12.0, 0.35, seed=1000 + k, reservoir=0)
+        masks.append(m)
+    Qs = [float(u) * int((m[0] == 0).sum()) for u, m in zip(umean, masks)]
+    return masks, Qs, edges
+
+
+def run_ensemble(stream, prec="fp16dev", steps=2000, warmup=64):
+    """Throughput of the batched ensemble step (one launch per step, graph
+    replay) and the step kernel's HBM roofline."""
+    import torch
+
+    from paper_1806_10589_gb300 import Batch
+
+    masks, Qs, edges = ensemble_workload()
+    with Batch(masks, TAU, "mrt", prec, stream=stream) as b:
+        for k, q in enumerate(Qs):
+            b.set_flux_bc(k, q)
+        b.step(warmup)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        k_ms = b.time_step(100)
+        n = b.info()["n_pore"]
+        fl = [b.get_flux(k, 4)[0] for k in range(len(masks))]
+    s = BYTES_PER_VALUE[prec]
+    peak, _ = measured_hbm_peak()
+    ach = 2 * 19 * s * n / (k_ms * 1e-3) / 1e9
+    return {"workload": "64 sphere packs, edges U{64..160} (%d..%d), porosity 0.35, tau 0.7, "
+                        "u_mean U[5e-5,2e-4], %s storage" % (int(edges.min()), int(edges.max()), prec),
+            "n_pore": n, "steps": steps, "MLUPS": round(n * steps / (ms * 1e-3) / 1e6, 1),
+            "ms_per_step": round(ms / steps, 5),
+            "roofline": {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(ach / peak, 4), "kernel": "k_batch_step", "kernel_ms": round(k_ms, 5),
+                         "bytes_per_unit": 2 * 19 * s},
+            "max_inlet_flux_rel_err": max(abs(f - q) / q for f, q in zip(fl, Qs))}
+
+
 # ------------------------------------------------------------- our path ---
 def run_ours(args, rank, world, local):
     import torch
@@ -288,6 +374,14 @@ def run_ours(args, rank, world, local):
     d2h = 4 * 8 * nx * ny * nz
     e2e_mlups = n * K / (t1 - t0) / 1e6
 
+    ens = None
+    if rank == 0 and args.ensemble:
+        ens = run_ensemble(stream)
+
+    steady = None
+    if rank == 0 and args.steady:
+        steady = time_to_steady(mask, a_in, stream)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         probe_mlups, _, _ = oracle_rate(mask[:16].copy(), 1)
@@ -315,12 +409,13 @@ def run_ours(args, rank, world, local):
                      "kernel": "k_step", "kernel_ms": round(ms_step_k, 5),
                      "bytes_per_unit": unit_bytes, "units_per_launch": n,
                      "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind
-                     if peak_kind == "measured" else "fallback 6.8 TB/s",
-                     "inlet_kernel_ms": round(ms_inlet_k, 5)},
+                     if peak_kind == "measured" else "fallback 6.8 TB/s"},
         "cpu_baseline": cpu,
         "e2e": {"value": round(e2e_mlups, 2), "unit": METRIC, "h2d_bytes_per_step": h2d / K,
                 "d2h_bytes_per_step": d2h / K},
-        "gpu_launches": 2 * K,
+        "gpu_launches": K + (2 * (K // 1024) if prec in ("fp16dev", "bf16dev") else 0),
+        "time_to_steady": steady,
+        "ensemble": ens,
         "clocks": clk,
         "check": {"q_in": q_in, "Q": Q, "rho_in": rho_in, "u_max": mon["u_max"], "status": mon["status"]},
     }
@@ -386,6 +481,10 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=list(BYTES_PER_VALUE), default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--steady", action=argparse.BooleanOptionalAction, default=True,
+                    help="also run the time-to-steady-flux comparison (FP32 / FP16 / BF16)")
+    ap.add_argument("--ensemble", action=argparse.BooleanOptionalAction, default=True,
+                    help="also time the batched 64-member ensemble (FP16 deviation storage)")
     ap.add_argument("--profile-case", action="store_true",
                     help="run the short fixed launch sequence used for ncu captures")
     args = ap.parse_args(argv)

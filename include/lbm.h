@@ -177,6 +177,39 @@ int lbm_inlet_density_noalloc(lbm_ctx* ctx, double* rho_in_device);
 /* Free all device and host memory of the context.  NULL is accepted. */
 int lbm_destroy(lbm_ctx* ctx);
 
+/* ---------------------------------------------------------------------------
+ * Batched ensemble: n_members independent sub-volumes (each its own voxel box,
+ * mask and inlet flux target, same tau/model/precision), advanced together by
+ * one kernel launch per step; runs of 64 steps replay a captured CUDA graph.
+ * Per member the problem is exactly the single-lattice one above (Section 2:
+ * flux inlet by Eq. potential + Appendix B closures, pressure outlet rho = 1,
+ * no-flow lateral faces, Appendix A collision).
+ * ------------------------------------------------------------------------- */
+typedef struct lbm_batch lbm_batch; /* opaque */
+
+/* masks: n_members host pointers to uint8 [z][y][x] masks (copied); dims: 3 ints
+ * per member (nx, ny, nz) with the single-lattice limits; every member needs
+ * pore nodes on its inlet and outlet planes.  Members start at rest with Q = 0. */
+int lbm_batch_create(int n_members, const uint8_t* const* masks, const int* dims, double tau, int model,
+                     int precision, lbm_batch** out);
+/* Inlet flux Q of one member (Eq. flux), as lbm_set_flux_bc.  Synchronises. */
+int lbm_batch_set_flux_bc(lbm_batch* b, int member, double Q);
+int lbm_batch_set_stream(lbm_batch* b, void* cuda_stream);
+/* Advance all members n >= 0 steps, asynchronously on the batch's stream. */
+int lbm_batch_step(lbm_batch* b, int n);
+/* As lbm_get_flux for one member (sum of u_z over the face, FP64; imposed density). */
+int lbm_batch_get_flux(lbm_batch* b, int member, int face, double* Q, double* rho_bc);
+/* One member's distributions to/from a host array of 19*nx*ny*nz doubles [q][z][y][x]. */
+int lbm_batch_get_distributions(lbm_batch* b, int member, double* f);
+int lbm_batch_set_distributions(lbm_batch* b, int member, const double* f);
+/* Total pore nodes, 256-node tiles of the launch, steps taken.  NULLs allowed. */
+int lbm_batch_get_info(const lbm_batch* b, int64_t* n_pore, int64_t* n_tiles, int64_t* steps);
+/* Profiling aid: n >= 1 single-step launches with CUDA events around each on the
+ * batch's stream; mean device milliseconds per step.  Advances the state. */
+int lbm_batch_time_step(lbm_batch* b, int n, float* ms);
+int lbm_batch_destroy(lbm_batch* b);
+const char* lbm_batch_last_error(const lbm_batch* b);
+
 /* Message of the last error on ctx (or of the last failed lbm_create when
  * ctx is NULL).  The string is owned by the library and valid until the next
  * call on the same context. */

@@ -29,6 +29,7 @@ constexpr int kGraphSteps = 64;  // steps per captured graph (even: parity prese
 #define LBM_DEFAULT_STEP_VARIANT 1
 #endif
 constexpr int kDefaultStepVariant = LBM_DEFAULT_STEP_VARIANT;
+constexpr int64_t kReencodeInterval = 1024;  // steps between 16-bit reference refreshes
 thread_local std::string g_create_error;
 
 }  // namespace
@@ -58,6 +59,8 @@ struct lbm_ctx {
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     int64_t steps = 0;
+    int64_t since_reencode = 0;  // steps since the 16-bit reference profile was refreshed
+    int ref_e = 0;               // profile slot the stored values are encoded with
     int status = LBM_OK;
     std::string err;
     std::vector<int64_t> pore_voxel;  // unpadded [z][y][x] index of each pore node
@@ -118,6 +121,17 @@ int prime_inlet(lbm_ctx* c) {
     return LBM_OK;
 }
 
+// 16-bit formats: refresh the reference density profile (re-encoding the
+// state) every kReencodeInterval steps, then recompute the inlet density from
+// the re-encoded values.  Asynchronous; a no-op for FP32/FP64.
+int maybe_reencode(lbm_ctx* c) {
+    if (c->prec < LBM_PREC_FP16DEV || c->since_reencode < kReencodeInterval) return LBM_OK;
+    LBM_CUDA(c, lbm::launch_reencode(c->prec, c->f[c->cur], c->L, c->d_bc, c->ref_e, c->cur, c->stream));
+    c->ref_e ^= 1;
+    c->since_reencode = 0;
+    return prime_inlet(c);
+}
+
 int build_graph(lbm_ctx* c, int parity) {
     const int saved = c->cur;
     c->cur = parity;
@@ -139,7 +153,7 @@ int build_graph(lbm_ctx* c, int parity) {
 }
 
 int run_monitors(lbm_ctx* c, lbm::MonitorOut* out) {
-    LBM_CUDA(c, lbm::launch_monitors(c->prec, c->f[c->cur], c->L, c->d_mon_partials, c->d_mon_counter,
+    LBM_CUDA(c, lbm::launch_monitors(c->prec, c->f[c->cur], c->L, c->d_bc, c->d_mon_partials, c->d_mon_counter,
                                      c->d_mon, c->stream));
     LBM_CUDA(c, cudaMemcpyAsync(out, c->d_mon, sizeof(*out), cudaMemcpyDeviceToHost, c->stream));
     LBM_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -266,6 +280,11 @@ int lbm_create(const uint8_t* mask, int nx, int ny, int nz, double tau, int mode
     c->L.sz = (int)(px * py);
     for (int q = 0; q < 19; ++q)
         c->L.goff[q] = -(lbm::cz(q) * c->L.sz + lbm::cy(q) * c->L.sy + lbm::cx(q));
+    {
+        const unsigned __int128 two64 = (unsigned __int128)1 << 64;
+        const unsigned __int128 szq = (unsigned __int128)(uint64_t)c->L.sz;
+        c->L.sz_magic = (uint64_t)(two64 / szq + (two64 % szq != 0 ? 1 : 0));
+    }
 
     // ---- device memory
     int rc = LBM_OK;
@@ -300,7 +319,7 @@ int lbm_create(const uint8_t* mask, int nx, int ny, int nz, double tau, int mode
     if (e == cudaSuccess) e = cudaMemset(c->f[1], 0, fbytes);
     c->h_bc = lbm::BcState{};
     if (e == cudaSuccess) e = cudaMemcpy(c->d_bc, &c->h_bc, sizeof(lbm::BcState), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = lbm::launch_init_eq(precision, c->f[0], c->L, nullptr, nullptr, nullptr, nullptr, 0);
+    if (e == cudaSuccess) e = lbm::launch_init_eq(precision, c->f[0], c->L, c->d_bc, nullptr, nullptr, nullptr, nullptr, 0);
     if (e == cudaSuccess)
         e = lbm::launch_inlet_reduce(precision, c->f[0], 0, c->L, c->d_bc, c->d_red_partials, c->d_red_counter, 0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -373,12 +392,17 @@ int lbm_step(lbm_ctx* c, int n) {
     if (n < 0) return fail(c, LBM_EINVAL, "n must be >= 0");
     int k = 0;
     while (n - k >= kGraphSteps) {
+        if ((rc = maybe_reencode(c))) return rc;
         if (!c->graph[c->cur] && (rc = build_graph(c, c->cur))) return rc;
         LBM_CUDA(c, cudaGraphLaunch(c->graph[c->cur], c->stream));
         k += kGraphSteps;
+        c->since_reencode += kGraphSteps;
     }
-    for (; k < n; ++k)
+    for (; k < n; ++k) {
+        if ((rc = maybe_reencode(c))) return rc;
         if ((rc = one_step(c, c->stream))) return rc;
+        ++c->since_reencode;
+    }
     c->steps += n;
     return LBM_OK;
 }
@@ -434,7 +458,7 @@ int lbm_steady_residual(lbm_ctx* c, double* residual) {
         if ((rc = dev_alloc(c, &c->d_u_ref, (size_t)3 * c->L.n * sizeof(double)))) return rc;
         LBM_CUDA(c, cudaMemsetAsync(c->d_u_ref, 0, (size_t)3 * c->L.n * sizeof(double), c->stream));
     }
-    LBM_CUDA(c, lbm::launch_velocity_change(c->prec, c->f[c->cur], c->L, c->d_u_ref, c->d_mon_partials,
+    LBM_CUDA(c, lbm::launch_velocity_change(c->prec, c->f[c->cur], c->L, c->d_bc, c->d_u_ref, c->d_mon_partials,
                                             c->d_mon_counter, c->d_mon, c->stream));
     lbm::MonitorOut m{};
     LBM_CUDA(c, cudaMemcpyAsync(&m, c->d_mon, sizeof m, cudaMemcpyDeviceToHost, c->stream));
@@ -471,7 +495,7 @@ int lbm_get_fields(lbm_ctx* c, double* rho, double* ux, double* uy, double* uz) 
     double* outs[4] = {rho, ux, uy, uz};
     cudaError_t e = cudaMemsetAsync(d, 0, 4 * ncell * sizeof(double), c->stream);
     if (e == cudaSuccess)
-        e = lbm::launch_export(c->prec, c->f[c->cur], c->L, d, d + ncell, d + 2 * ncell, d + 3 * ncell, 1,
+        e = lbm::launch_export(c->prec, c->f[c->cur], c->L, c->d_bc, d, d + ncell, d + 2 * ncell, d + 3 * ncell, 1,
                                c->stream);
     for (int k = 0; k < 4 && e == cudaSuccess; ++k)
         if (outs[k])
@@ -490,7 +514,7 @@ int lbm_get_fields_device(lbm_ctx* c, float* rho, float* u) {
     const size_t ncell = (size_t)c->nx * c->ny * c->nz;
     if (rho) LBM_CUDA(c, cudaMemsetAsync(rho, 0, ncell * sizeof(float), c->stream));
     if (u) LBM_CUDA(c, cudaMemsetAsync(u, 0, 3 * ncell * sizeof(float), c->stream));
-    LBM_CUDA(c, lbm::launch_export(c->prec, c->f[c->cur], c->L, rho, u, u ? u + ncell : nullptr,
+    LBM_CUDA(c, lbm::launch_export(c->prec, c->f[c->cur], c->L, c->d_bc, rho, u, u ? u + ncell : nullptr,
                                    u ? u + 2 * ncell : nullptr, 0, c->stream));
     return LBM_OK;
 }
@@ -508,7 +532,7 @@ int lbm_set_fields(lbm_ctx* c, const double* rho, const double* ux, const double
     if ((rc = dev_alloc(c, &d, h.size() * sizeof(double)))) return rc;
     cudaError_t e = cudaMemcpyAsync(d, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess)
-        e = lbm::launch_init_eq(c->prec, c->f[c->cur], c->L, rho ? d : nullptr, ux ? d + n : nullptr,
+        e = lbm::launch_init_eq(c->prec, c->f[c->cur], c->L, c->d_bc, rho ? d : nullptr, ux ? d + n : nullptr,
                                 uy ? d + 2 * n : nullptr, uz ? d + 3 * n : nullptr, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     cudaFree(d);
@@ -526,7 +550,7 @@ int lbm_get_distributions(lbm_ctx* c, double* f) {
     std::vector<double> h((size_t)(19 * n));
     double* d = nullptr;
     if ((rc = dev_alloc(c, &d, h.size() * sizeof(double)))) return rc;
-    cudaError_t e = lbm::launch_decode(c->prec, c->f[c->cur], c->L, d, c->stream);
+    cudaError_t e = lbm::launch_decode(c->prec, c->f[c->cur], c->L, c->d_bc, d, c->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(h.data(), d, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -556,7 +580,7 @@ int lbm_set_distributions(lbm_ctx* c, const double* f) {
     double* d = nullptr;
     if ((rc = dev_alloc(c, &d, h.size() * sizeof(double)))) return rc;
     cudaError_t e = cudaMemcpyAsync(d, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream);
-    if (e == cudaSuccess) e = lbm::launch_encode(c->prec, c->f[c->cur], c->L, d, c->stream);
+    if (e == cudaSuccess) e = lbm::launch_encode(c->prec, c->f[c->cur], c->L, c->d_bc, d, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     cudaFree(d);
     if (e != cudaSuccess) return fail(c, LBM_ECUDA, "lbm_set_distributions: %s", cudaGetErrorString(e));

@@ -1,0 +1,810 @@
+// Batched ensemble: many independent porous sub-volumes of uneven size, each
+// with its own flux target, advanced by ONE kernel launch per time step.
+//
+// All members share one structure-of-arrays distribution store.  Each member's
+// pore list (z, y, x order, inlet plane first, outlet plane last) starts on a
+// 256-node tile boundary, its padded id grid holds global pore indices, and a
+// per-tile member table routes every block to its member's parameters.  The
+// step is the single-lattice step (pull with halfway bounce-back, Appendix B
+// closures with the inlet density of Eq. potential, collision, store) with the
+// member's own boundary scalars; the next step's inlet density of every member
+// is formed in the same launch (FP64, deterministic last-tile finish per
+// member).  Runs of 64 steps replay a captured CUDA graph.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "lbm_device.cuh"
+#include "lbm_internal.h"
+
+namespace lbm {
+namespace {
+
+constexpr int kTile = 256;
+constexpr int kBatchGraphSteps = 64;
+constexpr int64_t kBatchReencodeInterval = 1024;
+
+// Per-member parameters and boundary state (device, mutable).
+struct Member {
+    int64_t base;       // first global pore slot (multiple of kTile)
+    int64_t n;          // pore nodes
+    int64_t a_in;       // inlet pore nodes: local [0, a_in)
+    int64_t a_out;      // outlet pore nodes: local [n - a_out, n)
+    int64_t a_01;       // pore nodes on planes z = 0, 1: local [0, a_01)
+    int64_t grid_base;  // first padded voxel of the member's id grid
+    uint64_t sz_magic;  // ceil(2^64 / ((nx+2)(ny+2)))
+    int nz;
+    int goff[19];       // padded-grid offsets of the pull sources
+    double Q;           // prescribed inlet flux
+    double drho_out;    // outlet density - 1
+    double drho_in[2];  // inlet density - 1 for the step reading buffer c
+    float ref_r0[2], ref_g[2];  // 16-bit reference profile slots
+    int ref_cur;
+};
+
+template <int... Qs, class F>
+__device__ __forceinline__ void for_q(std::integer_sequence<int, Qs...>, F&& f) {
+    (f(std::integral_constant<int, Qs>{}), ...);
+}
+using AllQ = std::make_integer_sequence<int, 19>;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (wid == 0) {
+        r = lane < kTile / 32 ? sh[lane] : 0.0;
+        r = warp_sum(r);
+    }
+    __syncthreads();
+    return r;
+}
+
+template <class S>
+__device__ __forceinline__ typename S::M member_ref(const Member& m, int64_t p_global) {
+    using M = typename S::M;
+    if constexpr (S::kRef) {
+        const int z = plane_of((uint64_t)(p_global - m.grid_base), m.sz_magic);
+        const int c = m.ref_cur;
+        return M(m.ref_r0[c]) + M(m.ref_g[c]) * M(z);
+    } else {
+        return M(0);
+    }
+}
+template <class S>
+__device__ __forceinline__ typename S::M member_slope(const Member& m) {
+    using M = typename S::M;
+    if constexpr (S::kRef) return M(m.ref_g[m.ref_cur]);
+    else return M(0);
+}
+
+template <class S, int Q>
+__device__ __forceinline__ typename S::M pull_b(const typename S::T* __restrict__ fin, int64_t ns,
+                                                const int* __restrict__ grid, const Member& m,
+                                                int64_t p, int64_t i, typename S::M r_own,
+                                                typename S::M g) {
+    using M = typename S::M;
+    if (Q == 0) return S::template dec<0>(fin[i], r_own);
+    const int id = __ldg(grid + p + m.goff[Q]);
+    if (id >= 0) return S::template dec<Q>(fin[(int64_t)Q * ns + id], r_own - M(cz(Q)) * g);
+    return S::template dec<Q>(fin[(int64_t)opp(Q) * ns + i], r_own);
+}
+
+// Same contribution rule as the single-lattice step (see lbm_kernels.cu).
+template <class S>
+__device__ __forceinline__ double next_inlet_part_b(const typename S::M* d, const int* __restrict__ grid,
+                                                    const Member& m, int64_t p, int64_t il,
+                                                    typename S::M r_own) {
+    double s = 0.0;
+    auto val = [&](auto qc) -> double {
+        constexpr int Q = decltype(qc)::value;
+        return (double)S::template dec<Q>(S::template enc<Q>(d[Q], r_own), r_own);
+    };
+    auto dest_is_pore = [&](auto qc) -> bool {
+        constexpr int Q = decltype(qc)::value;
+        return __ldg(grid + p + m.goff[opp(Q)]) >= 0;
+    };
+    if (il < m.a_in) {
+        for_q(std::integer_sequence<int, 0, 1, 2, 3, 4, 7, 8, 9, 10>{}, [&](auto qc) { s += val(qc); });
+        for_q(std::integer_sequence<int, 5, 11, 14, 15, 18>{},
+              [&](auto qc) { if (!dest_is_pore(qc)) s += 2.0 * val(qc); });
+    } else {
+        for_q(std::integer_sequence<int, 6, 12, 13, 16, 17>{},
+              [&](auto qc) { if (dest_is_pore(qc)) s += 2.0 * val(qc); });
+    }
+    return s;
+}
+
+// Per-member reduction of `part` over the member's tiles [0, ntiles_member):
+// partials per global tile, a ticket per member, the last tile writes.
+template <class F>
+__device__ __forceinline__ void member_reduce(double part, int64_t tile, int64_t tile0, int64_t ntm,
+                                              double* partials, unsigned* counter, double* sh, F&& finish) {
+    __shared__ bool last;
+    const double b = block_sum(part, sh);
+    if (threadIdx.x == 0) {
+        partials[tile] = b;
+        __threadfence();
+        last = atomicAdd(counter, 1u) == (unsigned)ntm - 1;
+    }
+    __syncthreads();
+    if (last) {
+        __threadfence();
+        double s = 0.0;
+        for (int64_t j = threadIdx.x; j < ntm; j += kTile) s += __ldcg(partials + tile0 + j);
+        s = block_sum(s, sh);
+        if (threadIdx.x == 0) {
+            finish(s);
+            *counter = 0u;
+        }
+    }
+}
+
+template <class S>
+__global__ void __launch_bounds__(kTile)
+k_batch_step(const typename S::T* __restrict__ fin, typename S::T* __restrict__ fout, int64_t ns, int slot,
+             const uint32_t* __restrict__ vox, const int* __restrict__ grid, const int* __restrict__ tile_member,
+             Member* members, typename S::M sp, typename S::M sm, double* __restrict__ partials,
+             unsigned* __restrict__ counters) {
+    using M = typename S::M;
+    __shared__ double sh[32];
+    const int64_t tile = blockIdx.x;
+    const int mi = tile_member[tile];
+    const Member& m = members[mi];
+    const int64_t tile0 = m.base / kTile;
+    const int64_t i = tile * kTile + threadIdx.x;
+    const int64_t il = i - m.base;
+    double part = 0.0;
+    if (il < m.n) {
+        const int64_t p = vox[i];
+        const M r_own = member_ref<S>(m, p), g = member_slope<S>(m);
+        M d[19];
+        for_q(AllQ{}, [&](auto qc) {
+            constexpr int Q = decltype(qc)::value;
+            d[Q] = pull_b<S, Q>(fin, ns, grid, m, p, i, r_own, g);
+        });
+        if (il < m.a_in) {
+            close_inlet(d, M(m.drho_in[slot]) - inlet_known(d));
+        } else if (il >= m.n - m.a_out) {
+            close_outlet(d, outlet_known(d) - M(m.drho_out));
+        }
+        collide(d, sp, sm);
+        for_q(AllQ{}, [&](auto qc) {
+            constexpr int Q = decltype(qc)::value;
+            fout[(int64_t)Q * ns + i] = S::template enc<Q>(d[Q], r_own);
+        });
+        if (il < m.a_01) part = next_inlet_part_b<S>(d, grid, m, p, il, r_own);
+    }
+    const int64_t nt01 = (m.a_01 + kTile - 1) / kTile;
+    if (tile - tile0 < nt01)
+        member_reduce(part, tile, tile0, nt01, partials, counters + mi, sh, [&](double s) {
+            members[mi].drho_in[slot ^ 1] = (m.Q + s) / (double)m.a_in;
+        });
+}
+
+// Inlet density of every member by a pull over its inlet plane (states set
+// from outside a step).  Grid: all tiles; tiles past a member's inlet exit.
+template <class S>
+__global__ void __launch_bounds__(kTile)
+k_batch_inlet(const typename S::T* __restrict__ fin, int64_t ns, int slot, const uint32_t* __restrict__ vox,
+              const int* __restrict__ grid, const int* __restrict__ tile_member, Member* members,
+              double* __restrict__ partials, unsigned* __restrict__ counters) {
+    using M = typename S::M;
+    __shared__ double sh[32];
+    const int64_t tile = blockIdx.x;
+    const int mi = tile_member[tile];
+    const Member& m = members[mi];
+    const int64_t tile0 = m.base / kTile;
+    const int64_t nti = (m.a_in + kTile - 1) / kTile;
+    if (tile - tile0 >= nti) return;  // block-uniform
+    const int64_t i = tile * kTile + threadIdx.x;
+    const int64_t il = i - m.base;
+    double k = 0.0;
+    if (il < m.a_in) {
+        const int64_t p = vox[i];
+        const M r_own = member_ref<S>(m, p), g = member_slope<S>(m);
+        M d[19];
+        for_q(std::integer_sequence<int, 0, 1, 2, 3, 4, 6, 7, 8, 9, 10, 12, 13, 16, 17>{}, [&](auto qc) {
+            constexpr int Q = decltype(qc)::value;
+            d[Q] = pull_b<S, Q>(fin, ns, grid, m, p, i, r_own, g);
+        });
+        k = (double)d[0] + (double)d[1] + (double)d[2] + (double)d[3] + (double)d[4] + (double)d[7] +
+            (double)d[8] + (double)d[9] + (double)d[10] +
+            2.0 * ((double)d[6] + (double)d[12] + (double)d[13] + (double)d[16] + (double)d[17]);
+    }
+    member_reduce(k, tile, tile0, nti, partials, counters + mi, sh, [&](double s) {
+        members[mi].drho_in[slot] = (m.Q + s) / (double)m.a_in;
+    });
+}
+
+// Sum of u_z over a member's inlet (which = 0) or outlet (which = 1) plane of
+// the stored state; grid = that member's tiles.
+template <class S>
+__global__ void __launch_bounds__(kTile)
+k_batch_face_flux(const typename S::T* __restrict__ f, int64_t ns, const uint32_t* __restrict__ vox,
+                  const Member* members, int mi, int which, double* __restrict__ partials,
+                  unsigned* __restrict__ counter, double* out) {
+    using M = typename S::M;
+    __shared__ double sh[32];
+    const Member& m = members[mi];
+    const int64_t tile0 = m.base / kTile;
+    const int64_t tile = tile0 + blockIdx.x;
+    const int64_t i = tile * kTile + threadIdx.x;
+    const int64_t il = i - m.base;
+    double v = 0.0;
+    const bool on = which == 0 ? il < m.a_in : (il >= m.n - m.a_out && il < m.n);
+    if (on) {
+        const M r_own = member_ref<S>(m, vox[i]);
+        M d[19];
+        for_q(AllQ{}, [&](auto qc) {
+            constexpr int Q = decltype(qc)::value;
+            d[Q] = S::template dec<Q>(f[(int64_t)Q * ns + i], r_own);
+        });
+        M drho, jx, jy, jz;
+        moments(d, drho, jx, jy, jz);
+        v = (double)jz;
+    }
+    member_reduce(v, tile, tile0, (int64_t)gridDim.x, partials, counter, sh, [&](double s) { *out = s; });
+}
+
+template <class S>
+__global__ void k_batch_reencode(typename S::T* __restrict__ f, int64_t ns, const uint32_t* __restrict__ vox,
+                                 const int* __restrict__ tile_member, Member* members, int e, int slot,
+                                 int64_t total) {
+    using M = typename S::M;
+    const int64_t i = (int64_t)blockIdx.x * kTile + threadIdx.x;
+    if (i >= total) return;
+    const int mi = tile_member[blockIdx.x];
+    Member& m = members[mi];
+    const float r0n = (float)m.drho_in[slot];
+    const float gn = (float)((m.drho_out - m.drho_in[slot]) / (double)(m.nz - 1));
+    const int64_t il = i - m.base;
+    if (il == 0) {
+        m.ref_r0[e ^ 1] = r0n;
+        m.ref_g[e ^ 1] = gn;
+        m.ref_cur = e ^ 1;
+    }
+    if (il >= m.n) return;
+    const int z = plane_of((uint64_t)(vox[i] - m.grid_base), m.sz_magic);
+    const M r_old = M(m.ref_r0[e]) + M(m.ref_g[e]) * M(z);
+    const M r_new = M(r0n) + M(gn) * M(z);
+    for_q(AllQ{}, [&](auto qc) {
+        constexpr int Q = decltype(qc)::value;
+        typename S::T* a = f + (int64_t)Q * ns + i;
+        *a = S::template enc<Q>(S::template dec<Q>(*a, r_old), r_new);
+    });
+}
+
+// d = f - w for one member, pore order, row stride n (double) <-> storage.
+template <class S>
+__global__ void k_batch_encode(typename S::T* __restrict__ f, int64_t ns, const uint32_t* __restrict__ vox,
+                               const Member* members, int mi, const double* __restrict__ d) {
+    const Member& m = members[mi];
+    const int64_t il = (int64_t)blockIdx.x * kTile + threadIdx.x;
+    if (il >= m.n) return;
+    const int64_t i = m.base + il;
+    const typename S::M r_own = member_ref<S>(m, vox[i]);
+    for_q(AllQ{}, [&](auto qc) {
+        constexpr int Q = decltype(qc)::value;
+        f[(int64_t)Q * ns + i] = S::template enc<Q>((typename S::M)d[(int64_t)Q * m.n + il], r_own);
+    });
+}
+template <class S>
+__global__ void k_batch_decode(const typename S::T* __restrict__ f, int64_t ns, const uint32_t* __restrict__ vox,
+                               const Member* members, int mi, double* __restrict__ d) {
+    const Member& m = members[mi];
+    const int64_t il = (int64_t)blockIdx.x * kTile + threadIdx.x;
+    if (il >= m.n) return;
+    const int64_t i = m.base + il;
+    const typename S::M r_own = member_ref<S>(m, vox[i]);
+    for_q(AllQ{}, [&](auto qc) {
+        constexpr int Q = decltype(qc)::value;
+        d[(int64_t)Q * m.n + il] = (double)S::template dec<Q>(f[(int64_t)Q * ns + i], r_own);
+    });
+}
+
+template <class F>
+cudaError_t dispatch(int prec, F&& f) {
+    switch (prec) {
+        case 0: return f(StoreF64{});
+        case 1: return f(StoreF32{});
+        case 2: return f(StoreF16{});
+        case 3: return f(StoreBF16{});
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+thread_local std::string g_batch_create_error;
+
+}  // namespace
+}  // namespace lbm
+
+struct lbm_batch {
+    int device = 0;
+    int prec = 1;
+    int nm = 0;
+    double sp = 1.0, sm = 1.0;
+    int64_t total = 0;   // global pore slots (multiple of the tile)
+    int64_t ns = 0;      // row stride
+    int64_t ntiles = 0;
+    void* f[2] = {nullptr, nullptr};
+    int cur = 0;
+    uint32_t* d_vox = nullptr;
+    int* d_grid = nullptr;
+    int* d_tile_member = nullptr;
+    lbm::Member* d_members = nullptr;
+    double* d_partials = nullptr;
+    unsigned* d_counters = nullptr;    // one per member (step and inlet reductions)
+    unsigned* d_counter1 = nullptr;    // face-flux reduction
+    double* d_out = nullptr;
+    std::vector<lbm::Member> h_members;
+    std::vector<std::vector<int64_t>> pore_voxel;  // per member: unpadded voxel of each pore
+    std::vector<int> dims;                          // 3 per member
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    int64_t steps = 0, since_reencode = 0;
+    int ref_e = 0;
+    int status = LBM_OK;
+    std::string err;
+};
+
+namespace {
+
+int bfail(lbm_batch* b, int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (b) {
+        b->err = buf;
+        if (code == LBM_ECUDA) b->status = LBM_ECUDA;
+    } else {
+        lbm::g_batch_create_error = buf;
+    }
+    return code;
+}
+
+#define BATCH_CUDA(b, call)                                                                \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return bfail((b), LBM_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));  \
+    } while (0)
+
+int benter(lbm_batch* b) {
+    if (!b) return LBM_EINVAL;
+    if (b->status == LBM_ECUDA) return LBM_ECUDA;
+    BATCH_CUDA(b, cudaSetDevice(b->device));
+    return LBM_OK;
+}
+
+void brelease(lbm_batch* b) {
+    for (auto& g : b->graph)
+        if (g) cudaGraphExecDestroy(g);
+    for (auto& p : b->f)
+        if (p) cudaFree(p);
+    cudaFree(b->d_vox);
+    cudaFree(b->d_grid);
+    cudaFree(b->d_tile_member);
+    cudaFree(b->d_members);
+    cudaFree(b->d_partials);
+    cudaFree(b->d_counters);
+    cudaFree(b->d_counter1);
+    cudaFree(b->d_out);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+}
+
+int bstep_once(lbm_batch* b, cudaStream_t st) {
+    cudaError_t e = lbm::dispatch(b->prec, [&](auto s) {
+        using S = decltype(s);
+        using T = typename S::T;
+        using M = typename S::M;
+        lbm::k_batch_step<S><<<(unsigned)b->ntiles, lbm::kTile, 0, st>>>(
+            (const T*)b->f[b->cur], (T*)b->f[b->cur ^ 1], b->ns, b->cur, b->d_vox, b->d_grid,
+            b->d_tile_member, b->d_members, (M)b->sp, (M)b->sm, b->d_partials, b->d_counters);
+        return cudaGetLastError();
+    });
+    BATCH_CUDA(b, e);
+    b->cur ^= 1;
+    return LBM_OK;
+}
+
+int bprime(lbm_batch* b) {
+    cudaError_t e = lbm::dispatch(b->prec, [&](auto s) {
+        using S = decltype(s);
+        using T = typename S::T;
+        lbm::k_batch_inlet<S><<<(unsigned)b->ntiles, lbm::kTile, 0, b->stream>>>(
+            (const T*)b->f[b->cur], b->ns, b->cur, b->d_vox, b->d_grid, b->d_tile_member, b->d_members,
+            b->d_partials, b->d_counters);
+        return cudaGetLastError();
+    });
+    BATCH_CUDA(b, e);
+    return LBM_OK;
+}
+
+int bmaybe_reencode(lbm_batch* b) {
+    if (b->prec < LBM_PREC_FP16DEV || b->since_reencode < lbm::kBatchReencodeInterval) return LBM_OK;
+    cudaError_t e = lbm::dispatch(b->prec, [&](auto s) {
+        using S = decltype(s);
+        using T = typename S::T;
+        if constexpr (S::kRef) {
+            lbm::k_batch_reencode<S><<<(unsigned)b->ntiles, lbm::kTile, 0, b->stream>>>(
+                (T*)b->f[b->cur], b->ns, b->d_vox, b->d_tile_member, b->d_members, b->ref_e, b->cur, b->total);
+        }
+        return cudaGetLastError();
+    });
+    BATCH_CUDA(b, e);
+    b->ref_e ^= 1;
+    b->since_reencode = 0;
+    return bprime(b);
+}
+
+int bbuild_graph(lbm_batch* b, int parity) {
+    const int saved = b->cur;
+    b->cur = parity;
+    cudaGraph_t g = nullptr;
+    BATCH_CUDA(b, cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+    int rc = LBM_OK;
+    for (int k = 0; k < lbm::kBatchGraphSteps && rc == LBM_OK; ++k) rc = bstep_once(b, b->cap_stream);
+    cudaError_t e = cudaStreamEndCapture(b->cap_stream, &g);
+    b->cur = saved;
+    if (rc != LBM_OK) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) return bfail(b, LBM_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&b->graph[parity], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return bfail(b, LBM_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    return LBM_OK;
+}
+
+int push_member(lbm_batch* b, int mi) {
+    BATCH_CUDA(b, cudaMemcpyAsync(b->d_members + mi, &b->h_members[(size_t)mi], sizeof(lbm::Member),
+                                  cudaMemcpyHostToDevice, b->stream));
+    BATCH_CUDA(b, cudaStreamSynchronize(b->stream));
+    return LBM_OK;
+}
+
+// Refresh the host copy of a member's device-side state (densities, profile).
+int pull_member(lbm_batch* b, int mi) {
+    BATCH_CUDA(b, cudaMemcpyAsync(&b->h_members[(size_t)mi], b->d_members + mi, sizeof(lbm::Member),
+                                  cudaMemcpyDeviceToHost, b->stream));
+    BATCH_CUDA(b, cudaStreamSynchronize(b->stream));
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_batch_create(int n_members, const uint8_t* const* masks, const int* dims, double tau, int model,
+                     int precision, lbm_batch** out) {
+    using lbm::g_batch_create_error;
+    g_batch_create_error.clear();
+    if (!out) return bfail(nullptr, LBM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n_members < 1 || n_members > 65535 || !masks || !dims)
+        return bfail(nullptr, LBM_EINVAL, "need 1..65535 members with masks and dims");
+    if (!(tau > 0.5) || !(tau < 1e6)) return bfail(nullptr, LBM_EINVAL, "tau=%g must exceed 0.5", tau);
+    if (model != LBM_MODEL_BGK && model != LBM_MODEL_MRT) return bfail(nullptr, LBM_EINVAL, "unknown model");
+    if (precision < LBM_PREC_FP64 || precision > LBM_PREC_BF16DEV)
+        return bfail(nullptr, LBM_EINVAL, "unknown precision");
+    auto* b = new (std::nothrow) lbm_batch();
+    if (!b) return bfail(nullptr, LBM_ENOMEM, "host allocation");
+    cudaGetDevice(&b->device);
+    b->prec = precision;
+    b->nm = n_members;
+    b->sp = 1.0 / tau;
+    b->sm = model == LBM_MODEL_MRT ? 8.0 * (2.0 - b->sp) / (8.0 - b->sp) : b->sp;
+    b->h_members.resize((size_t)n_members);
+    b->pore_voxel.resize((size_t)n_members);
+    b->dims.assign(dims, dims + 3 * n_members);
+
+    std::vector<int> grid;
+    std::vector<uint32_t> vox;
+    std::vector<int> tile_member;
+    int64_t base = 0, gbase = 0;
+    for (int mi = 0; mi < n_members; ++mi) {
+        const int nx = dims[3 * mi], ny = dims[3 * mi + 1], nz = dims[3 * mi + 2];
+        const uint8_t* mask = masks[mi];
+        if (!mask || nx < 1 || ny < 1 || nx > 2047 || ny > 2047 || nz < 3 || nz > 1023) {
+            delete b;
+            return bfail(nullptr, LBM_EINVAL, "member %d: bad mask or box %dx%dx%d", mi, nx, ny, nz);
+        }
+        const int64_t px = nx + 2, py = ny + 2, pz = nz + 2;
+        const int64_t pad = px * py * pz;
+        if (gbase + pad > (int64_t)UINT32_MAX) {
+            delete b;
+            return bfail(nullptr, LBM_EINVAL, "padded boxes exceed 2^32 voxels in total");
+        }
+        grid.resize((size_t)(gbase + pad), lbm::SOLID);
+        for (int64_t y = 0; y < py; ++y)
+            for (int64_t x = 0; x < px; ++x) {
+                grid[(size_t)(gbase + y * px + x)] = lbm::ZOUT;
+                grid[(size_t)(gbase + ((pz - 1) * py + y) * px + x)] = lbm::ZOUT;
+            }
+        lbm::Member m{};
+        m.base = base;
+        m.grid_base = gbase;
+        m.nz = nz;
+        int64_t a_in = 0, a_out = 0, a_01 = 0, n = 0;
+        for (int64_t z = 0; z < nz; ++z)
+            for (int64_t y = 0; y < ny; ++y)
+                for (int64_t x = 0; x < nx; ++x) {
+                    const int64_t v = (z * ny + y) * nx + x;
+                    if (mask[v] > 1) {
+                        delete b;
+                        return bfail(nullptr, LBM_EINVAL, "member %d: mask value %d (must be 0 or 1)", mi, mask[v]);
+                    }
+                    if (mask[v]) continue;
+                    const int64_t p = ((z + 1) * py + (y + 1)) * px + (x + 1);
+                    grid[(size_t)(gbase + p)] = (int)(base + n);
+                    vox.push_back((uint32_t)(gbase + p));
+                    b->pore_voxel[(size_t)mi].push_back(v);
+                    ++n;
+                    if (z == 0) ++a_in;
+                    if (z == nz - 1) ++a_out;
+                    if (z <= 1) ++a_01;
+                }
+        if (a_in == 0 || a_out == 0) {
+            delete b;
+            return bfail(nullptr, LBM_EINVAL, "member %d: inlet and outlet planes need pore nodes", mi);
+        }
+        m.n = n;
+        m.a_in = a_in;
+        m.a_out = a_out;
+        m.a_01 = a_01;
+        for (int q = 0; q < 19; ++q) m.goff[q] = (int)(-(lbm::cz(q) * px * py + lbm::cy(q) * px + lbm::cx(q)));
+        const unsigned __int128 two64 = (unsigned __int128)1 << 64;
+        const unsigned __int128 szq = (unsigned __int128)(uint64_t)(px * py);
+        m.sz_magic = (uint64_t)(two64 / szq + (two64 % szq != 0 ? 1 : 0));
+        b->h_members[(size_t)mi] = m;
+        const int64_t nt = (n + lbm::kTile - 1) / lbm::kTile;
+        for (int64_t t = 0; t < nt; ++t) tile_member.push_back(mi);
+        vox.resize((size_t)(base + nt * lbm::kTile), 0u);
+        base += nt * lbm::kTile;
+        gbase += pad;
+        if (base >= INT32_MAX) {
+            delete b;
+            return bfail(nullptr, LBM_EINVAL, "more than 2^31-1 pore slots in total");
+        }
+    }
+    b->total = base;
+    b->ntiles = base / lbm::kTile;
+    b->ns = (base + 127) / 128 * 128;
+    const size_t fbytes = (size_t)19 * (size_t)b->ns * (size_t)lbm::elem_size(precision);
+    cudaError_t e = cudaSuccess;
+    auto A = [&](auto** p, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMalloc((void**)p, bytes);
+    };
+    A(&b->f[0], fbytes);
+    A(&b->f[1], fbytes);
+    A(&b->d_vox, vox.size() * 4);
+    A(&b->d_grid, grid.size() * 4);
+    A(&b->d_tile_member, tile_member.size() * 4);
+    A(&b->d_members, (size_t)n_members * sizeof(lbm::Member));
+    A(&b->d_partials, (size_t)b->ntiles * sizeof(double));
+    A(&b->d_counters, (size_t)n_members * sizeof(unsigned));
+    A(&b->d_counter1, sizeof(unsigned));
+    A(&b->d_out, sizeof(double));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_vox, vox.data(), vox.size() * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_grid, grid.data(), grid.size() * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->d_tile_member, tile_member.data(), tile_member.size() * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->d_members, b->h_members.data(), (size_t)n_members * sizeof(lbm::Member),
+                       cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(b->d_counters, 0, (size_t)n_members * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(b->d_counter1, 0, sizeof(unsigned));
+    // rest state: d = f - w = 0 in every format (the reference profile starts at 0)
+    if (e == cudaSuccess) e = cudaMemset(b->f[0], 0, fbytes);
+    if (e == cudaSuccess) e = cudaMemset(b->f[1], 0, fbytes);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        bfail(nullptr, e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA, "lbm_batch_create: %s",
+              cudaGetErrorString(e));
+        cudaGetLastError();
+        brelease(b);
+        delete b;
+        return e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA;
+    }
+    int rc = bprime(b);
+    if (rc == LBM_OK && cudaDeviceSynchronize() != cudaSuccess) rc = LBM_ECUDA;
+    if (rc != LBM_OK) {
+        g_batch_create_error = b->err;
+        brelease(b);
+        delete b;
+        return rc;
+    }
+    *out = b;
+    return LBM_OK;
+}
+
+int lbm_batch_set_stream(lbm_batch* b, void* s) {
+    int rc = benter(b);
+    if (rc) return rc;
+    b->stream = (cudaStream_t)s;
+    return LBM_OK;
+}
+
+int lbm_batch_set_flux_bc(lbm_batch* b, int member, double Q) {
+    int rc = benter(b);
+    if (rc) return rc;
+    if (member < 0 || member >= b->nm) return bfail(b, LBM_EINVAL, "member %d out of range", member);
+    if (!(Q == Q) || Q > 1e30 || Q < -1e30) return bfail(b, LBM_EINVAL, "Q must be finite");
+    if ((rc = pull_member(b, member))) return rc;
+    b->h_members[(size_t)member].Q = Q;
+    if ((rc = push_member(b, member))) return rc;
+    return bprime(b);
+}
+
+int lbm_batch_step(lbm_batch* b, int n) {
+    int rc = benter(b);
+    if (rc) return rc;
+    if (n < 0) return bfail(b, LBM_EINVAL, "n must be >= 0");
+    int k = 0;
+    while (n - k >= lbm::kBatchGraphSteps) {
+        if ((rc = bmaybe_reencode(b))) return rc;
+        if (!b->graph[b->cur] && (rc = bbuild_graph(b, b->cur))) return rc;
+        BATCH_CUDA(b, cudaGraphLaunch(b->graph[b->cur], b->stream));
+        k += lbm::kBatchGraphSteps;
+        b->since_reencode += lbm::kBatchGraphSteps;
+    }
+    for (; k < n; ++k) {
+        if ((rc = bmaybe_reencode(b))) return rc;
+        if ((rc = bstep_once(b, b->stream))) return rc;
+        ++b->since_reencode;
+    }
+    b->steps += n;
+    return LBM_OK;
+}
+
+int lbm_batch_time_step(lbm_batch* b, int n, float* ms) {
+    int rc = benter(b);
+    if (rc) return rc;
+    if (n < 1) return bfail(b, LBM_EINVAL, "n must be >= 1");
+    cudaEvent_t e0, e1;
+    BATCH_CUDA(b, cudaEventCreate(&e0));
+    BATCH_CUDA(b, cudaEventCreate(&e1));
+    double tot = 0.0;
+    for (int k = 0; k < n; ++k) {
+        BATCH_CUDA(b, cudaEventRecord(e0, b->stream));
+        if ((rc = bstep_once(b, b->stream))) return rc;
+        BATCH_CUDA(b, cudaEventRecord(e1, b->stream));
+        BATCH_CUDA(b, cudaEventSynchronize(e1));
+        float t = 0.f;
+        BATCH_CUDA(b, cudaEventElapsedTime(&t, e0, e1));
+        tot += t;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->steps += n;
+    b->since_reencode += n;
+    if (ms) *ms = (float)(tot / n);
+    return LBM_OK;
+}
+
+int lbm_batch_get_flux(lbm_batch* b, int member, int face, double* Q, double* rho_bc) {
+    int rc = benter(b);
+    if (rc) return rc;
+    if (member < 0 || member >= b->nm) return bfail(b, LBM_EINVAL, "member %d out of range", member);
+    if (face != LBM_FACE_ZMIN && face != LBM_FACE_ZMAX) return bfail(b, LBM_EINVAL, "unknown face %d", face);
+    if ((rc = pull_member(b, member))) return rc;
+    const lbm::Member& m = b->h_members[(size_t)member];
+    const unsigned nt = (unsigned)((m.n + lbm::kTile - 1) / lbm::kTile);
+    cudaError_t e = lbm::dispatch(b->prec, [&](auto s) {
+        using S = decltype(s);
+        lbm::k_batch_face_flux<S><<<nt, lbm::kTile, 0, b->stream>>>(
+            (const typename S::T*)b->f[b->cur], b->ns, b->d_vox, b->d_members, member,
+            face == LBM_FACE_ZMIN ? 0 : 1, b->d_partials, b->d_counter1, b->d_out);
+        return cudaGetLastError();
+    });
+    BATCH_CUDA(b, e);
+    double q = 0.0;
+    BATCH_CUDA(b, cudaMemcpyAsync(&q, b->d_out, sizeof q, cudaMemcpyDeviceToHost, b->stream));
+    BATCH_CUDA(b, cudaStreamSynchronize(b->stream));
+    if (Q) *Q = q;
+    if (rho_bc) *rho_bc = 1.0 + (face == LBM_FACE_ZMAX ? m.drho_out : m.drho_in[b->cur ^ 1]);
+    return LBM_OK;
+}
+
+int lbm_batch_get_distributions(lbm_batch* b, int member, double* f) {
+    int rc = benter(b);
+    if (rc) return rc;
+    if (member < 0 || member >= b->nm || !f) return bfail(b, LBM_EINVAL, "bad member or NULL f");
+    const lbm::Member& m = b->h_members[(size_t)member];
+    const size_t ncell = (size_t)b->dims[3 * member] * b->dims[3 * member + 1] * b->dims[3 * member + 2];
+    std::vector<double> h((size_t)(19 * m.n));
+    double* d = nullptr;
+    BATCH_CUDA(b, cudaMalloc(&d, h.size() * sizeof(double)));
+    cudaError_t e = lbm::dispatch(b->prec, [&](auto s) {
+        using S = decltype(s);
+        lbm::k_batch_decode<S><<<(unsigned)((m.n + lbm::kTile - 1) / lbm::kTile), lbm::kTile, 0, b->stream>>>(
+            (const typename S::T*)b->f[b->cur], b->ns, b->d_vox, b->d_members, member, d);
+        return cudaGetLastError();
+    });
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h.data(), d, h.size() * sizeof(double), cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    cudaFree(d);
+    if (e != cudaSuccess) return bfail(b, LBM_ECUDA, "lbm_batch_get_distributions: %s", cudaGetErrorString(e));
+    std::memset(f, 0, 19 * ncell * sizeof(double));
+    const auto& pv = b->pore_voxel[(size_t)member];
+    for (int q = 0; q < 19; ++q)
+        for (int64_t i = 0; i < m.n; ++i)
+            f[(size_t)q * ncell + (size_t)pv[(size_t)i]] = lbm::wq(q) + h[(size_t)(q * m.n + i)];
+    return LBM_OK;
+}
+
+int lbm_batch_set_distributions(lbm_batch* b, int member, const double* f) {
+    int rc = benter(b);
+    if (rc) return rc;
+    if (member < 0 || member >= b->nm || !f) return bfail(b, LBM_EINVAL, "bad member or NULL f");
+    if ((rc = pull_member(b, member))) return rc;
+    const lbm::Member& m = b->h_members[(size_t)member];
+    const size_t ncell = (size_t)b->dims[3 * member] * b->dims[3 * member + 1] * b->dims[3 * member + 2];
+    const auto& pv = b->pore_voxel[(size_t)member];
+    std::vector<double> h((size_t)(19 * m.n));
+    for (int q = 0; q < 19; ++q)
+        for (int64_t i = 0; i < m.n; ++i)
+            h[(size_t)(q * m.n + i)] = f[(size_t)q * ncell + (size_t)pv[(size_t)i]] - lbm::wq(q);
+    double* d = nullptr;
+    BATCH_CUDA(b, cudaMalloc(&d, h.size() * sizeof(double)));
+    cudaError_t e = cudaMemcpyAsync(d, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess)
+        e = lbm::dispatch(b->prec, [&](auto s) {
+            using S = decltype(s);
+            lbm::k_batch_encode<S><<<(unsigned)((m.n + lbm::kTile - 1) / lbm::kTile), lbm::kTile, 0, b->stream>>>(
+                (typename S::T*)b->f[b->cur], b->ns, b->d_vox, b->d_members, member, d);
+            return cudaGetLastError();
+        });
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    cudaFree(d);
+    if (e != cudaSuccess) return bfail(b, LBM_ECUDA, "lbm_batch_set_distributions: %s", cudaGetErrorString(e));
+    return bprime(b);
+}
+
+int lbm_batch_get_info(const lbm_batch* b, int64_t* n_pore, int64_t* n_tiles, int64_t* steps) {
+    if (!b) return LBM_EINVAL;
+    int64_t n = 0;
+    for (const auto& m : b->h_members) n += m.n;
+    if (n_pore) *n_pore = n;
+    if (n_tiles) *n_tiles = b->ntiles;
+    if (steps) *steps = b->steps;
+    return LBM_OK;
+}
+
+int lbm_batch_destroy(lbm_batch* b) {
+    if (!b) return LBM_OK;
+    cudaSetDevice(b->device);
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    brelease(b);
+    delete b;
+    return LBM_OK;
+}
+
+const char* lbm_batch_last_error(const lbm_batch* b) {
+    return b ? b->err.c_str() : lbm::g_batch_create_error.c_str();
+}
+
+}  // extern "C"

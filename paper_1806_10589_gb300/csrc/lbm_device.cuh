@@ -44,40 +44,49 @@ constexpr int SOLID = -1;
 constexpr int ZOUT = -2;
 
 // ----------------------------------------------------------------- codecs ---
-// Storage of d_q.  FP64 / FP32 store d_q; the 16-bit formats store
-// (d_q / w_q) * 2^10 = (f_q / w_q - 1) * 2^10.
+// Storage of d_q.  FP64 / FP32 store d_q.  The 16-bit formats store
+//     (d_q / w_q - r) * 2^10 = (f_q / w_q - 1 - r) * 2^10,
+// the deviation from the weight scaled to the reference density 1 + r of the
+// plane z of the node that WROTE the value, r = r0 + g z (a linear profile
+// between the inlet and outlet densities, refreshed by re-encoding).  Removing
+// the mean pressure gradient leaves the local deviation, so the 11 (FP16) or 8
+// (BF16) significant bits resolve the velocity part instead of the density ramp.
 constexpr float DEV_SCALE = 1024.0f;
 
 struct StoreF64 {
     using T = double;
     using M = double;
-    template <int Q> __device__ static M dec(T v) { return v; }
-    template <int Q> __device__ static T enc(M v) { return v; }
+    static constexpr bool kRef = false;
+    template <int Q> __device__ static M dec(T v, M) { return v; }
+    template <int Q> __device__ static T enc(M v, M) { return v; }
 };
 struct StoreF32 {
     using T = float;
     using M = float;
-    template <int Q> __device__ static M dec(T v) { return v; }
-    template <int Q> __device__ static T enc(M v) { return v; }
+    static constexpr bool kRef = false;
+    template <int Q> __device__ static M dec(T v, M) { return v; }
+    template <int Q> __device__ static T enc(M v, M) { return v; }
 };
 struct StoreF16 {
     using T = __half;
     using M = float;
-    template <int Q> __device__ static M dec(T v) {
-        return __half2float(v) * float(wq(Q) / 1024.0);
+    static constexpr bool kRef = true;
+    template <int Q> __device__ static M dec(T v, M r) {
+        return float(wq(Q)) * fmaf(__half2float(v), 1.0f / 1024.0f, r);
     }
-    template <int Q> __device__ static T enc(M v) {
-        return __float2half_rn(v * float(1024.0 / wq(Q)));
+    template <int Q> __device__ static T enc(M v, M r) {
+        return __float2half_rn(fmaf(v, float(1.0 / wq(Q)), -r) * 1024.0f);
     }
 };
 struct StoreBF16 {
     using T = __nv_bfloat16;
     using M = float;
-    template <int Q> __device__ static M dec(T v) {
-        return __bfloat162float(v) * float(wq(Q) / 1024.0);
+    static constexpr bool kRef = true;
+    template <int Q> __device__ static M dec(T v, M r) {
+        return float(wq(Q)) * fmaf(__bfloat162float(v), 1.0f / 1024.0f, r);
     }
-    template <int Q> __device__ static T enc(M v) {
-        return __float2bfloat16_rn(v * float(1024.0 / wq(Q)));
+    template <int Q> __device__ static T enc(M v, M r) {
+        return __float2bfloat16_rn(fmaf(v, float(1.0 / wq(Q)), -r) * 1024.0f);
     }
 };
 
@@ -93,7 +102,28 @@ struct BcState {
     int inlet_mode;        // 0 = flux (Eq. potential), 1 = fixed pressure
     int pad_;
     double drho_in[2];     // per buffer parity, see above
+    // Reference density profile r(z) = r0 + g z of the 16-bit formats, two
+    // slots: ref_cur selects the one the stored values are encoded with.
+    float ref_r0[2];
+    float ref_g[2];
+    int ref_cur;
+    int pad2_;
 };
+
+// Plane z of a padded voxel index p = ((z+1)(ny+2) + y+1)(nx+2) + x+1, with
+// magic = ceil(2^64 / ((nx+2)(ny+2))): exact for p < 2^32.
+__device__ __forceinline__ int plane_of(uint64_t p, uint64_t magic) {
+    return (int)__umul64hi(p, magic) - 1;
+}
+template <class M>
+__device__ __forceinline__ M ref_at(const BcState* bc, int z) {
+    const int c = bc->ref_cur;
+    return M(bc->ref_r0[c]) + M(bc->ref_g[c]) * M(z);
+}
+template <class M>
+__device__ __forceinline__ M ref_slope(const BcState* bc) {
+    return M(bc->ref_g[bc->ref_cur]);
+}
 
 // ------------------------------------------------------- cache hints ---
 // L2 eviction-priority hints (PTX createpolicy / .L2::cache_hint): the streamed
@@ -164,14 +194,17 @@ __device__ __forceinline__ int64_t grid_off(int sy, int sz) {
 
 // Pull one direction: d~_q(i) = d_q(src) for a pore source, own d_opp(i) for a
 // solid (halfway bounce-back) or z-outside source (overwritten by the closure).
+// r_own / g: reference profile at the node's plane and its slope; a pulled
+// value was written on plane z - xi_z, where the reference is r_own - g xi_z.
 template <class S, int Q>
 __device__ __forceinline__ typename S::M pull(const typename S::T* __restrict__ fin, int64_t ns,
                                               const int* __restrict__ grid, int64_t p, int i,
-                                              int sy, int sz) {
-    if (Q == 0) return S::template dec<0>(fin[i]);
+                                              int sy, int sz, typename S::M r_own, typename S::M g) {
+    using M = typename S::M;
+    if (Q == 0) return S::template dec<0>(fin[i], r_own);
     const int id = __ldg(grid + p + grid_off<Q>(sy, sz));
-    if (id >= 0) return S::template dec<Q>(fin[(int64_t)Q * ns + id]);
-    return S::template dec<Q>(fin[(int64_t)opp(Q) * ns + i]);
+    if (id >= 0) return S::template dec<Q>(fin[(int64_t)Q * ns + id], r_own - M(cz(Q)) * g);
+    return S::template dec<Q>(fin[(int64_t)opp(Q) * ns + i], r_own);
 }
 
 // Known-sum of Eq. (inlet) on shifted values: K' = K - 1 (the weights of the

@@ -21,6 +21,7 @@ struct DevLattice {
     const uint32_t* vox;  // [n] padded linear voxel index of each pore node
     const int* grid;      // [(nz+2)(ny+2)(nx+2)] padded id grid
     int goff[19];         // padded-grid offset of the pull source x - xi_q, per q
+    uint64_t sz_magic;    // ceil(2^64 / sz): plane of a padded voxel index
 };
 
 struct Relax {
@@ -56,16 +57,21 @@ cudaError_t configure_step(int prec, int variant, const DevLattice& L, StepConfi
 cudaError_t launch_step_cfg(int prec, const StepConfig& cfg, const void* fin, void* fout, int slot,
                             const DevLattice& L, Relax r, BcState* bc, double* partials, unsigned* counter,
                             cudaStream_t st);
-cudaError_t launch_monitors(int prec, const void* f, const DevLattice& L, double* partials,
+cudaError_t launch_monitors(int prec, const void* f, const DevLattice& L, const BcState* bc, double* partials,
                             unsigned* counter, MonitorOut* out, cudaStream_t st);
-cudaError_t launch_velocity_change(int prec, const void* f, const DevLattice& L, double* u_ref,
+cudaError_t launch_velocity_change(int prec, const void* f, const DevLattice& L, const BcState* bc, double* u_ref,
                                    double* partials, unsigned* counter, MonitorOut* out, cudaStream_t st);
-cudaError_t launch_export(int prec, const void* f, const DevLattice& L, void* rho, void* ux,
+cudaError_t launch_export(int prec, const void* f, const DevLattice& L, const BcState* bc, void* rho, void* ux,
                           void* uy, void* uz, int out_double, cudaStream_t st);
-cudaError_t launch_init_eq(int prec, void* f, const DevLattice& L, const double* rho,
+cudaError_t launch_init_eq(int prec, void* f, const DevLattice& L, const BcState* bc, const double* rho,
                            const double* ux, const double* uy, const double* uz, cudaStream_t st);
-cudaError_t launch_encode(int prec, void* f, const DevLattice& L, const double* d, cudaStream_t st);
-cudaError_t launch_decode(int prec, const void* f, const DevLattice& L, double* d, cudaStream_t st);
+cudaError_t launch_encode(int prec, void* f, const DevLattice& L, const BcState* bc, const double* d,
+                          cudaStream_t st);
+cudaError_t launch_decode(int prec, const void* f, const DevLattice& L, const BcState* bc, double* d,
+                          cudaStream_t st);
+// 16-bit formats: move the stored values to a new reference profile (no-op otherwise).
+cudaError_t launch_reencode(int prec, void* f, const DevLattice& L, BcState* bc, int e, int slot,
+                            cudaStream_t st);
 
 // No-allocation inlet density (lbm_noalloc.cu): scratch in a static device array.
 cudaError_t launch_inlet_density_noalloc(int prec, const void* fin, const DevLattice& L,

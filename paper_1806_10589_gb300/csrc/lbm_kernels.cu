@@ -40,13 +40,19 @@ __device__ __forceinline__ void for_q(std::integer_sequence<int, Qs...>, F&& f) 
 }
 using AllQ = std::make_integer_sequence<int, 19>;
 
+// Reference profile of the 16-bit formats at the plane of padded voxel p, and
+// its slope (both 0 for the formats that store d directly).
 template <class S>
-__device__ __forceinline__ void pull_all(typename S::M* d, const typename S::T* __restrict__ fin,
-                                         const DevLattice& L, int64_t p, int i) {
-    for_q(AllQ{}, [&](auto qc) {
-        constexpr int Q = decltype(qc)::value;
-        d[Q] = pull<S, Q>(fin, L.ns, L.grid, p, i, L.sy, L.sz);
-    });
+__device__ __forceinline__ typename S::M own_ref(const BcState* bc, const DevLattice& L, int64_t p) {
+    using M = typename S::M;
+    if constexpr (S::kRef) return ref_at<M>(bc, plane_of((uint64_t)p, L.sz_magic));
+    else return M(0);
+}
+template <class S>
+__device__ __forceinline__ typename S::M own_slope(const BcState* bc) {
+    using M = typename S::M;
+    if constexpr (S::kRef) return ref_slope<M>(bc);
+    else return M(0);
 }
 
 // ---------------------------------------------------- step-kernel access ---
@@ -99,34 +105,28 @@ __device__ __forceinline__ void st_stream(T* a, T v, uint64_t pol) {
 template <class S>
 __device__ __forceinline__ void pull_step(typename S::M* d, const StepPtrs<typename S::T>& P,
                                           const DevLattice& L, int64_t p, int i, uint64_t pol_f,
-                                          uint64_t pol_idx) {
+                                          uint64_t pol_idx, typename S::M r_own, typename S::M g) {
+    using M = typename S::M;
     for_q(AllQ{}, [&](auto qc) {
         constexpr int Q = decltype(qc)::value;
         if constexpr (Q == 0) {
-            d[0] = S::template dec<0>(ld_stream(P.in[0] + i, pol_f));
+            d[0] = S::template dec<0>(ld_stream(P.in[0] + i, pol_f), r_own);
         } else {
             const int id = ld_index(L.grid + p + L.goff[Q], pol_idx);
             const typename S::T* a = id >= 0 ? P.in[Q] + id : P.in[opp(Q)] + i;
-            d[Q] = S::template dec<Q>(ld_stream(a, pol_f));
+            // a pulled value was written on plane z - xi_z (reference r_own - g xi_z)
+            const M r = (cz(Q) != 0 && id >= 0) ? r_own - M(cz(Q)) * g : r_own;
+            d[Q] = S::template dec<Q>(ld_stream(a, pol_f), r);
         }
     });
 }
 
 template <class S>
 __device__ __forceinline__ void store_step(const typename S::M* d, const StepPtrs<typename S::T>& P,
-                                           int i, uint64_t pol_f) {
+                                           int i, uint64_t pol_f, typename S::M r_own) {
     for_q(AllQ{}, [&](auto qc) {
         constexpr int Q = decltype(qc)::value;
-        st_stream(P.out[Q] + i, S::template enc<Q>(d[Q]), pol_f);
-    });
-}
-
-template <class S>
-__device__ __forceinline__ void store_all(const typename S::M* d, typename S::T* __restrict__ fout,
-                                          int64_t ns, int i) {
-    for_q(AllQ{}, [&](auto qc) {
-        constexpr int Q = decltype(qc)::value;
-        fout[(int64_t)Q * ns + i] = S::template enc<Q>(d[Q]);
+        st_stream(P.out[Q] + i, S::template enc<Q>(d[Q], r_own), pol_f);
     });
 }
 
@@ -231,11 +231,12 @@ k_inlet_reduce(const typename S::T* __restrict__ fin, int slot, DevLattice L, Bc
         const int i = (int)i64;
         const int64_t p = L.vox[i];
         using M = typename S::M;
+        const M r_own = own_ref<S>(bc, L, p), g = own_slope<S>(bc);
         M d[19];
         for_q(std::integer_sequence<int, 0, 1, 2, 3, 4, 6, 7, 8, 9, 10, 12, 13, 16, 17>{},
               [&](auto qc) {
                   constexpr int Q = decltype(qc)::value;
-                  d[Q] = pull<S, Q>(fin, L.ns, L.grid, p, i, L.sy, L.sz);
+                  d[Q] = pull<S, Q>(fin, L.ns, L.grid, p, i, L.sy, L.sz, r_own, g);
               });
         k = (double)d[0] + (double)d[1] + (double)d[2] + (double)d[3] + (double)d[4] +
             (double)d[7] + (double)d[8] + (double)d[9] + (double)d[10] +
@@ -271,11 +272,11 @@ k_inlet_reduce(const typename S::T* __restrict__ fin, int slot, DevLattice L, Bc
 // Values are taken as the next step will decode them from storage.
 template <class S>
 __device__ __forceinline__ double next_inlet_part(const typename S::M* d, const DevLattice& L,
-                                                  int64_t p, int i) {
+                                                  int64_t p, int i, typename S::M r_own) {
     double s = 0.0;
     auto val = [&](auto qc) -> double {
         constexpr int Q = decltype(qc)::value;
-        return (double)S::template dec<Q>(S::template enc<Q>(d[Q]));
+        return (double)S::template dec<Q>(S::template enc<Q>(d[Q], r_own), r_own);
     };
     auto dest_is_pore = [&](auto qc) -> bool {
         constexpr int Q = decltype(qc)::value;  // destination i + xi_Q = pull source of opp(Q)
@@ -315,8 +316,9 @@ k_step(const StepPtrs<typename S::T> P, int slot, DevLattice L, typename S::M sp
         const uint64_t pol_idx = 0;
 #endif
         const int64_t p = ld_index(L.vox + i, pol_idx);
+        const M r_own = own_ref<S>(bc, L, p), g = own_slope<S>(bc);
         M d[19];
-        pull_step<S>(d, P, L, p, i, pol_f, pol_idx);
+        pull_step<S>(d, P, L, p, i, pol_f, pol_idx, r_own, g);
         if (i < L.a_in) {
             // Section 2: after streaming, before collision.  u_z from Eq. (inlet)
             // with the density of Eq. (potential); then the Appendix B closure.
@@ -327,8 +329,8 @@ k_step(const StepPtrs<typename S::T> P, int slot, DevLattice L, typename S::M sp
             close_outlet(d, uz);
         }
         collide(d, sp, sm);
-        store_step<S>(d, P, i, pol_f);
-        if (i64 < L.a_01) part = next_inlet_part<S>(d, L, p, i);
+        store_step<S>(d, P, i, pol_f, r_own);
+        if (i64 < L.a_01) part = next_inlet_part<S>(d, L, p, i, r_own);
     }
     // blocks that hold plane z = 0 or z = 1 nodes (block-uniform branch)
     if ((int64_t)blockIdx.x * kBlock < L.a_01) {
@@ -405,10 +407,11 @@ __device__ __forceinline__ void issue_ids(int* ids, const DevLattice& L, uint32_
 // of 16-bit values that sit in the upper half of their fetched 4-byte pair.
 template <class S, int NT>
 __device__ __forceinline__ unsigned issue_vals(unsigned char* vals, const int* ids,
-                                               const StepPtrs<typename S::T>& P, int i) {
+                                               const StepPtrs<typename S::T>& P, int i, unsigned& nbr) {
     using T = typename S::T;
     constexpr int SB = AsyncSlot<S>::kBytes;
     unsigned hi = 0;
+    nbr = 0;
     for_q(AllQ{}, [&](auto qc) {
         constexpr int Q = decltype(qc)::value;
         const T* a;
@@ -417,6 +420,7 @@ __device__ __forceinline__ unsigned issue_vals(unsigned char* vals, const int* i
         } else {
             const int id = ids[(Q - 1) * NT + threadIdx.x];
             a = id >= 0 ? P.in[Q] + id : P.in[opp(Q)] + i;
+            if constexpr (S::kRef && cz(Q) != 0) nbr |= (unsigned)(id >= 0) << Q;
         }
         const unsigned dst = smem_u32(vals + ((size_t)Q * NT + threadIdx.x) * SB);
         if constexpr (sizeof(T) == 2) {
@@ -431,17 +435,20 @@ __device__ __forceinline__ unsigned issue_vals(unsigned char* vals, const int* i
 }
 
 template <class S, int NT>
-__device__ __forceinline__ void read_vals(typename S::M* d, const unsigned char* vals, unsigned hi) {
+__device__ __forceinline__ void read_vals(typename S::M* d, const unsigned char* vals, unsigned hi,
+                                          unsigned nbr, typename S::M r_own, typename S::M g) {
     using T = typename S::T;
+    using M = typename S::M;
     constexpr int SB = AsyncSlot<S>::kBytes;
     for_q(AllQ{}, [&](auto qc) {
         constexpr int Q = decltype(qc)::value;
         const unsigned char* slot = vals + ((size_t)Q * NT + threadIdx.x) * SB;
+        const M r = (cz(Q) != 0 && ((nbr >> Q) & 1u)) ? r_own - M(cz(Q)) * g : r_own;
         if constexpr (sizeof(T) == 2) {
             const T* pair = reinterpret_cast<const T*>(slot);
-            d[Q] = S::template dec<Q>(pair[(hi >> Q) & 1u]);
+            d[Q] = S::template dec<Q>(pair[(hi >> Q) & 1u], r);
         } else {
-            d[Q] = S::template dec<Q>(*reinterpret_cast<const T*>(slot));
+            d[Q] = S::template dec<Q>(*reinterpret_cast<const T*>(slot), r);
         }
     });
 }
@@ -476,8 +483,8 @@ k_step_async(const StepPtrs<typename S::T> P, int slot, DevLattice L, typename S
     if (node(t) < L.n) issue_ids<NT>(ids, L, p_cur, pol_idx);
     cp_async_commit();
     cp_async_wait_all();
-    unsigned hi_cur = 0, hi_next = 0;
-    if (node(t) < L.n) hi_cur = issue_vals<S, NT>(vals0, ids, P, (int)node(t));
+    unsigned hi_cur = 0, hi_next = 0, nb_cur = 0, nb_next = 0;
+    if (node(t) < L.n) hi_cur = issue_vals<S, NT>(vals0, ids, P, (int)node(t), nb_cur);
     cp_async_commit();
     if (t + G < ntiles && node(t + G) < L.n) issue_ids<NT>(ids, L, p_next, pol_idx);
     cp_async_commit();
@@ -487,7 +494,7 @@ k_step_async(const StepPtrs<typename S::T> P, int slot, DevLattice L, typename S
         unsigned char* vnext = (k & 1) ? vals0 : vals1;
         cp_async_wait_all();  // B(t) and A(t + G) have landed
         const int64_t tn = t + G, tn2 = t + 2 * G;
-        if (tn < ntiles && node(tn) < L.n) hi_next = issue_vals<S, NT>(vnext, ids, P, (int)node(tn));
+        if (tn < ntiles && node(tn) < L.n) hi_next = issue_vals<S, NT>(vnext, ids, P, (int)node(tn), nb_next);
         cp_async_commit();
         if (tn2 < ntiles && node(tn2) < L.n) issue_ids<NT>(ids, L, p_next2, pol_idx);
         cp_async_commit();
@@ -499,8 +506,9 @@ k_step_async(const StepPtrs<typename S::T> P, int slot, DevLattice L, typename S
         double part = 0.0;
         if (i64 < L.n) {
             const int i = (int)i64;
+            const M r_own = own_ref<S>(bc, L, p_cur), g = own_slope<S>(bc);
             M d[19];
-            read_vals<S, NT>(d, vcur, hi_cur);
+            read_vals<S, NT>(d, vcur, hi_cur, nb_cur, r_own, g);
             if (i < L.a_in) {
                 const M drin = bc->inlet_mode ? M(bc->drho_in_fixed) : M(bc->drho_in[slot]);
                 close_inlet(d, drin - inlet_known(d));
@@ -511,9 +519,9 @@ k_step_async(const StepPtrs<typename S::T> P, int slot, DevLattice L, typename S
             collide(d, sp, sm);
             for_q(AllQ{}, [&](auto qc) {
                 constexpr int Q = decltype(qc)::value;
-                P.out[Q][i] = S::template enc<Q>(d[Q]);
+                P.out[Q][i] = S::template enc<Q>(d[Q], r_own);
             });
-            if (i64 < L.a_01) part = next_inlet_part<S>(d, L, p_cur, i);
+            if (i64 < L.a_01) part = next_inlet_part<S>(d, L, p_cur, i, r_own);
         }
         if (t < nt01) {  // tile holds plane z = 0 / z = 1 nodes (block-uniform)
             const double b = block_sum<NT>(part, sh);
@@ -535,6 +543,7 @@ k_step_async(const StepPtrs<typename S::T> P, int slot, DevLattice L, typename S
             }
         }
         hi_cur = hi_next;
+        nb_cur = nb_next;
         p_cur = p_next;
         p_next = p_next2;
         p_next2 = p_after;
@@ -545,8 +554,8 @@ k_step_async(const StepPtrs<typename S::T> P, int slot, DevLattice L, typename S
 // ---------------------------------------------------------- monitors ---
 template <class S>
 __global__ void __launch_bounds__(kReduceBlock)
-k_monitors(const typename S::T* __restrict__ f, DevLattice L, double* __restrict__ partials,
-           unsigned* __restrict__ counter, MonitorOut* out) {
+k_monitors(const typename S::T* __restrict__ f, DevLattice L, const BcState* bc,
+           double* __restrict__ partials, unsigned* __restrict__ counter, MonitorOut* out) {
     using M = typename S::M;
     __shared__ double sh[32];
     __shared__ bool last;
@@ -554,10 +563,11 @@ k_monitors(const typename S::T* __restrict__ f, DevLattice L, double* __restrict
     M v[5] = {M(0), M(0), M(0), M(0), M(0)};
     if (i64 < L.n) {
         const int i = (int)i64;
+        const M r_own = own_ref<S>(bc, L, L.vox[i]);
         M d[19];
         for_q(AllQ{}, [&](auto qc) {
             constexpr int Q = decltype(qc)::value;
-            d[Q] = S::template dec<Q>(f[(int64_t)Q * L.ns + i]);
+            d[Q] = S::template dec<Q>(f[(int64_t)Q * L.ns + i], r_own);
         });
         M drho, jx, jy, jz;
         moments(d, drho, jx, jy, jz);
@@ -612,7 +622,8 @@ k_monitors(const typename S::T* __restrict__ f, DevLattice L, double* __restrict
 // (|.| the Euclidean norm per node), FP64; u_ref <- u(t) for the next call.
 template <class S>
 __global__ void __launch_bounds__(kReduceBlock)
-k_velocity_change(const typename S::T* __restrict__ f, DevLattice L, double* __restrict__ u_ref,
+k_velocity_change(const typename S::T* __restrict__ f, DevLattice L, const BcState* bc,
+                  double* __restrict__ u_ref,
                   double* __restrict__ partials, unsigned* __restrict__ counter, MonitorOut* out) {
     using M = typename S::M;
     __shared__ double sh[32];
@@ -620,10 +631,11 @@ k_velocity_change(const typename S::T* __restrict__ f, DevLattice L, double* __r
     const int64_t i64 = (int64_t)blockIdx.x * kReduceBlock + threadIdx.x;
     M dn = M(0), un = M(0);
     if (i64 < L.n) {
+        const M r_own = own_ref<S>(bc, L, L.vox[i64]);
         M d[19];
         for_q(AllQ{}, [&](auto qc) {
             constexpr int Q = decltype(qc)::value;
-            d[Q] = S::template dec<Q>(f[(int64_t)Q * L.ns + i64]);
+            d[Q] = S::template dec<Q>(f[(int64_t)Q * L.ns + i64], r_own);
         });
         M drho, jx, jy, jz;
         moments(d, drho, jx, jy, jz);
@@ -664,6 +676,33 @@ k_velocity_change(const typename S::T* __restrict__ f, DevLattice L, double* __r
     }
 }
 
+// ---------------------------------------------------------- re-encode ---
+// 16-bit formats: move the reference profile to r(z) = r0 + g z with r0 = the
+// inlet density of the next step (drho_in[slot]) and g from there to the
+// outlet density, re-encoding every stored value in place (each node owns its
+// values).  Reads profile slot e, writes slot e ^ 1 and selects it.
+template <class S>
+__global__ void k_reencode(typename S::T* __restrict__ f, DevLattice L, BcState* bc, int e, int slot) {
+    using M = typename S::M;
+    const float r0n = (float)bc->drho_in[slot];
+    const float gn = (float)((bc->drho_out - bc->drho_in[slot]) / (double)(L.nz - 1));
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) {
+        bc->ref_r0[e ^ 1] = r0n;
+        bc->ref_g[e ^ 1] = gn;
+        bc->ref_cur = e ^ 1;
+    }
+    if (i >= L.n) return;
+    const int z = plane_of((uint64_t)L.vox[i], L.sz_magic);
+    const M r_old = M(bc->ref_r0[e]) + M(bc->ref_g[e]) * M(z);
+    const M r_new = M(r0n) + M(gn) * M(z);
+    for_q(AllQ{}, [&](auto qc) {
+        constexpr int Q = decltype(qc)::value;
+        typename S::T* a = f + (int64_t)Q * L.ns + i;
+        *a = S::template enc<Q>(S::template dec<Q>(*a, r_old), r_new);
+    });
+}
+
 // ---------------------------------------------------- conversions ---
 __device__ __forceinline__ int64_t unpadded(const DevLattice& L, int64_t p) {
     const int64_t z = p / L.sz - 1;
@@ -674,15 +713,16 @@ __device__ __forceinline__ int64_t unpadded(const DevLattice& L, int64_t p) {
 }
 
 template <class S, class O>
-__global__ void k_export(const typename S::T* __restrict__ f, DevLattice L, O* rho, O* ux, O* uy,
-                         O* uz) {
+__global__ void k_export(const typename S::T* __restrict__ f, DevLattice L, const BcState* bc, O* rho,
+                         O* ux, O* uy, O* uz) {
     using M = typename S::M;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= L.n) return;
+    const M r_own = own_ref<S>(bc, L, L.vox[i]);
     M d[19];
     for_q(AllQ{}, [&](auto qc) {
         constexpr int Q = decltype(qc)::value;
-        d[Q] = S::template dec<Q>(f[(int64_t)Q * L.ns + i]);
+        d[Q] = S::template dec<Q>(f[(int64_t)Q * L.ns + i], r_own);
     });
     M drho, jx, jy, jz;
     moments(d, drho, jx, jy, jz);
@@ -694,11 +734,12 @@ __global__ void k_export(const typename S::T* __restrict__ f, DevLattice L, O* r
 }
 
 template <class S>
-__global__ void k_init_eq(typename S::T* __restrict__ f, DevLattice L, const double* rho,
+__global__ void k_init_eq(typename S::T* __restrict__ f, DevLattice L, const BcState* bc, const double* rho,
                           const double* ux, const double* uy, const double* uz) {
     using M = typename S::M;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= L.n) return;
+    const M r_own = own_ref<S>(bc, L, L.vox[i]);
     const M dr = rho ? M(rho[i] - 1.0) : M(0);
     const M u[3] = {ux ? M(ux[i]) : M(0), uy ? M(uy[i]) : M(0), uz ? M(uz[i]) : M(0)};
     const M uu15 = M(1.5) * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
@@ -706,27 +747,31 @@ __global__ void k_init_eq(typename S::T* __restrict__ f, DevLattice L, const dou
         constexpr int Q = decltype(qc)::value;
         const M xu = M(cx(Q)) * u[0] + M(cy(Q)) * u[1] + M(cz(Q)) * u[2];
         const M dq = M(wq(Q)) * (dr + M(3) * xu + M(4.5) * xu * xu - uu15);
-        f[(int64_t)Q * L.ns + i] = S::template enc<Q>(dq);
+        f[(int64_t)Q * L.ns + i] = S::template enc<Q>(dq, r_own);
     });
 }
 
 template <class S>
-__global__ void k_encode(typename S::T* __restrict__ f, DevLattice L, const double* __restrict__ d) {
+__global__ void k_encode(typename S::T* __restrict__ f, DevLattice L, const BcState* bc,
+                         const double* __restrict__ d) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= L.n) return;
+    const typename S::M r_own = own_ref<S>(bc, L, L.vox[i]);
     for_q(AllQ{}, [&](auto qc) {
         constexpr int Q = decltype(qc)::value;
-        f[(int64_t)Q * L.ns + i] = S::template enc<Q>((typename S::M)d[(int64_t)Q * L.n + i]);
+        f[(int64_t)Q * L.ns + i] = S::template enc<Q>((typename S::M)d[(int64_t)Q * L.n + i], r_own);
     });
 }
 
 template <class S>
-__global__ void k_decode(const typename S::T* __restrict__ f, DevLattice L, double* __restrict__ d) {
+__global__ void k_decode(const typename S::T* __restrict__ f, DevLattice L, const BcState* bc,
+                         double* __restrict__ d) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= L.n) return;
+    const typename S::M r_own = own_ref<S>(bc, L, L.vox[i]);
     for_q(AllQ{}, [&](auto qc) {
         constexpr int Q = decltype(qc)::value;
-        d[(int64_t)Q * L.n + i] = (double)S::template dec<Q>(f[(int64_t)Q * L.ns + i]);
+        d[(int64_t)Q * L.n + i] = (double)S::template dec<Q>(f[(int64_t)Q * L.ns + i], r_own);
     });
 }
 
@@ -809,61 +854,76 @@ cudaError_t config_async_t(int* grid, int64_t n) {
     return cudaSuccess;
 }
 
-cudaError_t launch_monitors(int prec, const void* f, const DevLattice& L, double* partials,
+cudaError_t launch_monitors(int prec, const void* f, const DevLattice& L, const BcState* bc, double* partials,
                             unsigned* counter, MonitorOut* out, cudaStream_t st) {
     return dispatch(prec, [&](auto s) {
         using S = decltype(s);
-        k_monitors<S><<<monitor_blocks(L), kReduceBlock, 0, st>>>((const typename S::T*)f, L,
+        k_monitors<S><<<monitor_blocks(L), kReduceBlock, 0, st>>>((const typename S::T*)f, L, bc,
                                                                    partials, counter, out);
         return cudaGetLastError();
     });
 }
 
-cudaError_t launch_velocity_change(int prec, const void* f, const DevLattice& L, double* u_ref,
+cudaError_t launch_velocity_change(int prec, const void* f, const DevLattice& L, const BcState* bc, double* u_ref,
                                    double* partials, unsigned* counter, MonitorOut* out, cudaStream_t st) {
     return dispatch(prec, [&](auto s) {
         using S = decltype(s);
-        k_velocity_change<S><<<monitor_blocks(L), kReduceBlock, 0, st>>>((const typename S::T*)f, L, u_ref,
+        k_velocity_change<S><<<monitor_blocks(L), kReduceBlock, 0, st>>>((const typename S::T*)f, L, bc, u_ref,
                                                                          partials, counter, out);
         return cudaGetLastError();
     });
 }
 
-cudaError_t launch_export(int prec, const void* f, const DevLattice& L, void* rho, void* ux,
+cudaError_t launch_reencode(int prec, void* f, const DevLattice& L, BcState* bc, int e, int slot,
+                            cudaStream_t st) {
+    return dispatch(prec, [&](auto s) {
+        using S = decltype(s);
+        if constexpr (S::kRef) {
+            k_reencode<S><<<blocks_for(L.n, 256), 256, 0, st>>>((typename S::T*)f, L, bc, e, slot);
+            return cudaGetLastError();
+        } else {
+            return cudaSuccess;
+        }
+    });
+}
+
+cudaError_t launch_export(int prec, const void* f, const DevLattice& L, const BcState* bc, void* rho, void* ux,
                           void* uy, void* uz, int out_double, cudaStream_t st) {
     return dispatch(prec, [&](auto s) {
         using S = decltype(s);
         if (out_double)
             k_export<S, double><<<blocks_for(L.n, 256), 256, 0, st>>>(
-                (const typename S::T*)f, L, (double*)rho, (double*)ux, (double*)uy, (double*)uz);
+                (const typename S::T*)f, L, bc, (double*)rho, (double*)ux, (double*)uy, (double*)uz);
         else
             k_export<S, float><<<blocks_for(L.n, 256), 256, 0, st>>>(
-                (const typename S::T*)f, L, (float*)rho, (float*)ux, (float*)uy, (float*)uz);
+                (const typename S::T*)f, L, bc, (float*)rho, (float*)ux, (float*)uy, (float*)uz);
         return cudaGetLastError();
     });
 }
 
-cudaError_t launch_init_eq(int prec, void* f, const DevLattice& L, const double* rho,
+cudaError_t launch_init_eq(int prec, void* f, const DevLattice& L, const BcState* bc, const double* rho,
                            const double* ux, const double* uy, const double* uz, cudaStream_t st) {
     return dispatch(prec, [&](auto s) {
         using S = decltype(s);
-        k_init_eq<S><<<blocks_for(L.n, 256), 256, 0, st>>>((typename S::T*)f, L, rho, ux, uy, uz);
+        k_init_eq<S><<<blocks_for(L.n, 256), 256, 0, st>>>((typename S::T*)f, L, bc, rho, ux, uy, uz);
         return cudaGetLastError();
     });
 }
 
-cudaError_t launch_encode(int prec, void* f, const DevLattice& L, const double* d, cudaStream_t st) {
+cudaError_t launch_encode(int prec, void* f, const DevLattice& L, const BcState* bc, const double* d,
+                          cudaStream_t st) {
     return dispatch(prec, [&](auto s) {
         using S = decltype(s);
-        k_encode<S><<<blocks_for(L.n, 256), 256, 0, st>>>((typename S::T*)f, L, d);
+        k_encode<S><<<blocks_for(L.n, 256), 256, 0, st>>>((typename S::T*)f, L, bc, d);
         return cudaGetLastError();
     });
 }
 
-cudaError_t launch_decode(int prec, const void* f, const DevLattice& L, double* d, cudaStream_t st) {
+cudaError_t launch_decode(int prec, const void* f, const DevLattice& L, const BcState* bc, double* d,
+                          cudaStream_t st) {
     return dispatch(prec, [&](auto s) {
         using S = decltype(s);
-        k_decode<S><<<blocks_for(L.n, 256), 256, 0, st>>>((const typename S::T*)f, L, d);
+        k_decode<S><<<blocks_for(L.n, 256), 256, 0, st>>>((const typename S::T*)f, L, bc, d);
         return cudaGetLastError();
     });
 }

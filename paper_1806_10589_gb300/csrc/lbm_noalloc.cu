@@ -78,11 +78,16 @@ k_inlet_density_noalloc(const typename S::T* __restrict__ fin, DevLattice L, con
         const int i = (int)i64;
         const int64_t p = L.vox[i];
         using M = typename S::M;
+        M r_own = M(0), g = M(0);
+        if constexpr (S::kRef) {
+            r_own = ref_at<M>(bc, plane_of((uint64_t)p, L.sz_magic));
+            g = ref_slope<M>(bc);
+        }
         M d[19];
         for_each_q(std::integer_sequence<int, 0, 1, 2, 3, 4, 6, 7, 8, 9, 10, 12, 13, 16, 17>{},
                    [&](auto qc) {
                        constexpr int Q = decltype(qc)::value;
-                       d[Q] = pull<S, Q>(fin, L.ns, L.grid, p, i, L.sy, L.sz);
+                       d[Q] = pull<S, Q>(fin, L.ns, L.grid, p, i, L.sy, L.sz, r_own, g);
                    });
         k = (double)d[0] + (double)d[1] + (double)d[2] + (double)d[3] + (double)d[4] +
             (double)d[7] + (double)d[8] + (double)d[9] + (double)d[10] +

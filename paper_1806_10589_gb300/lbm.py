@@ -53,6 +53,18 @@ SIGNATURES = {
     "lbm_inlet_density_noalloc": (C.c_int, [_P, _P]),
     "lbm_destroy": (C.c_int, [_P]),
     "lbm_last_error": (C.c_char_p, [_P]),
+    "lbm_batch_create": (C.c_int, [C.c_int, C.POINTER(C.POINTER(C.c_uint8)), C.POINTER(C.c_int), C.c_double,
+                                   C.c_int, C.c_int, C.POINTER(_P)]),
+    "lbm_batch_set_flux_bc": (C.c_int, [_P, C.c_int, C.c_double]),
+    "lbm_batch_set_stream": (C.c_int, [_P, _P]),
+    "lbm_batch_step": (C.c_int, [_P, C.c_int]),
+    "lbm_batch_get_flux": (C.c_int, [_P, C.c_int, C.c_int, _DP, _DP]),
+    "lbm_batch_get_distributions": (C.c_int, [_P, C.c_int, _DP]),
+    "lbm_batch_set_distributions": (C.c_int, [_P, C.c_int, _DP]),
+    "lbm_batch_get_info": (C.c_int, [_P, _I64P, _I64P, _I64P]),
+    "lbm_batch_time_step": (C.c_int, [_P, C.c_int, _FP]),
+    "lbm_batch_destroy": (C.c_int, [_P]),
+    "lbm_batch_last_error": (C.c_char_p, [_P]),
 }
 
 _lib = None
@@ -226,3 +238,81 @@ class Lattice:
         a, b = C.c_float(), C.c_float()
         self._check(self._lib.lbm_time_kernels(self._h, int(n), C.byref(a), C.byref(b)))
         return a.value, b.value
+
+
+class Batch:
+    """A batched ensemble (lbm_batch_*): masks is a list of uint8 [z][y][x] arrays."""
+
+    def __init__(self, masks, tau, model="mrt", precision="fp16dev", stream=None):
+        lib = load_library()
+        self._masks = [np.ascontiguousarray(m, dtype=np.uint8) for m in masks]
+        n = len(self._masks)
+        ptrs = (C.POINTER(C.c_uint8) * n)(*[_ptr(m, C.c_uint8) for m in self._masks])
+        dims = (C.c_int * (3 * n))(*[v for m in self._masks for v in (m.shape[2], m.shape[1], m.shape[0])])
+        h = _P()
+        st = lib.lbm_batch_create(n, ptrs, dims, float(tau),
+                                  MODELS[model] if isinstance(model, str) else int(model),
+                                  PRECISIONS[precision] if isinstance(precision, str) else int(precision),
+                                  C.byref(h))
+        if st != LBM_OK:
+            raise LBMError(st, lib.lbm_batch_last_error(None).decode())
+        self._h, self._lib = h, lib
+        if stream is not None:
+            hs = getattr(stream, "cuda_stream", stream)
+            self._check(lib.lbm_batch_set_stream(h, _P(hs) if hs else None))
+
+    def _check(self, st):
+        if st != LBM_OK:
+            raise LBMError(st, self._lib.lbm_batch_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.lbm_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __len__(self):
+        return len(self._masks)
+
+    def set_flux_bc(self, member, Q):
+        self._check(self._lib.lbm_batch_set_flux_bc(self._h, int(member), float(Q)))
+
+    def step(self, n=1):
+        self._check(self._lib.lbm_batch_step(self._h, int(n)))
+
+    def get_flux(self, member, face=LBM_FACE_ZMIN):
+        q, r = C.c_double(), C.c_double()
+        self._check(self._lib.lbm_batch_get_flux(self._h, int(member), face, C.byref(q), C.byref(r)))
+        return q.value, r.value
+
+    def distributions(self, member):
+        f = np.empty((19,) + self._masks[member].shape)
+        self._check(self._lib.lbm_batch_get_distributions(self._h, int(member), _ptr(f, C.c_double)))
+        return f
+
+    def set_distributions(self, member, f):
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        if f.shape != (19,) + self._masks[member].shape:
+            raise ValueError("f must have shape (19,) + mask.shape")
+        self._check(self._lib.lbm_batch_set_distributions(self._h, int(member), _ptr(f, C.c_double)))
+
+    def info(self):
+        v = [C.c_int64() for _ in range(3)]
+        self._check(self._lib.lbm_batch_get_info(self._h, *[C.byref(x) for x in v]))
+        return dict(zip(("n_pore", "n_tiles", "steps"), (x.value for x in v)))
+
+    def time_step(self, n):
+        ms = C.c_float()
+        self._check(self._lib.lbm_batch_time_step(self._h, int(n), C.byref(ms)))
+        return ms.value

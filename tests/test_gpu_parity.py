@@ -313,3 +313,26 @@ def test_step_variants_agree_bitwise_on_interior(torch_cuda):
     outs = [_run_variant(m, 0.8, "fp32", 1, v, torch_cuda, seed=11)[1] for v in (0, 1, 2)]
     np.testing.assert_array_equal(outs[0], outs[1])
     np.testing.assert_array_equal(outs[0], outs[2])
+
+
+@pytest.mark.parametrize("prec", ["fp16dev", "bf16dev"])
+def test_16bit_reference_refresh_keeps_state_and_flux(torch_cuda, prec):
+    """Crossing a reference-profile refresh (every 1024 steps) of the 16-bit
+    formats: the flux through the inlet stays exact to the storage rounding and
+    the state stays close to the FP32 run of the same problem."""
+    m = duct_mask(10, 9, 40)
+    Q = 2e-3 * int((m[0] == 0).sum())
+    res = {}
+    for p in ("fp32", prec):
+        with _lat(m, 0.8, "mrt", p, torch_cuda) as lat:
+            lat.set_flux_bc(Q)
+            lat.step(1100)
+            q_in, rho_in = lat.get_flux(4)
+            res[p] = (lat.fields(), q_in, rho_in)
+    (rho32, _, _, uz32), _, rin32 = res["fp32"]
+    (rho16, _, _, uz16), q16, rin16 = res[prec]
+    bits = 11 if prec == "fp16dev" else 8
+    dmax = float(np.abs(rho32[m == 0] - 1).max())
+    assert abs(q16 - Q) <= 64 * 2.0 ** -bits * dmax * int((m[0] == 0).sum()) / 19
+    assert np.abs(uz16 - uz32).max() <= 0.2 * np.abs(uz32).max() * (2.0 ** (11 - bits))
+    assert abs(rin16 - rin32) <= 0.05 * abs(rin32 - 1)
