@@ -454,6 +454,55 @@ def run_reference(args, rank, world, local):
     print(json.dumps(line), flush=True)
 
 
+def run_warmstart(args):
+    """Learned warm start experiment: train the network on LBM steady states of
+    seeded 64^3 sphere packs (radii U[8,16], porosity U[0.25,0.45]) computed by
+    this library, then compare steps and wall time to the 0.1 % steady rule
+    from a cold and from a warm start on a larger seeded pack."""
+    import torch
+
+    from paper_1806_10589_gb300 import Batch, Lattice, WarmStartNet, convergence as cv, warmstart as ws
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    rng = np.random.default_rng(11)
+    S, side = args.ws_samples, 64
+    t0 = time.perf_counter()
+    masks = [sphere_pack(side, 8.0, 16.0, float(rng.uniform(0.25, 0.45)), seed=5000 + k)[0] for k in range(S)]
+    t_geo = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    targets, ks = ws.steady_targets(Batch, masks, TAU, UBAR, args.ws_lbm_steps, stream=stream)
+    torch.cuda.synchronize()
+    t_lbm = time.perf_counter() - t0
+    c_kc = ws.fit_kc(masks, ks)
+    net = WarmStartNet(8, 16, 32, stream=stream)
+    net.set_params(ws.he_init(net, seed=4))
+    ntr = int(0.9 * S)
+    t0 = time.perf_counter()
+    hist = net.train(np.stack(masks[:ntr]), targets[:ntr], epochs=args.ws_epochs, batch=8, lr=1e-3, seed=1)
+    t_train = time.perf_counter() - t0
+    val_loss = float(np.mean([net.loss_grad(np.stack(masks[j:j + 1]), targets[j:j + 1])[0]
+                              for j in range(ntr, S)]))
+    test_mask, _ = sphere_pack(args.ws_test, 8.0, 16.0, 0.35, seed=777)
+    A = int((test_mask[0] == 0).sum())
+    Q = UBAR * A
+    with Lattice(test_mask, TAU, "mrt", "fp32", stream=stream) as lat:
+        lat.set_flux_bc(Q)
+        ref = cv.run_to_residual(lat, Q, TAU, lag=1000, tol=1e-6, max_steps=args.ws_ref_steps,
+                                 sync=torch.cuda.synchronize)
+    res = ws.warm_vs_cold(Lattice, net, test_mask, Q, TAU, c_kc, ref["k"], stream=stream,
+                          sync=torch.cuda.synchronize, max_steps=args.ws_ref_steps)
+    out = {"warmstart": {
+        "train": {"samples": S, "side": side, "lbm_steps": args.ws_lbm_steps, "epochs": args.ws_epochs,
+                  "loss_first": float(hist[0]), "loss_last": float(hist[-1]), "val_loss": val_loss,
+                  "c_kc": c_kc, "seconds": {"geometry": round(t_geo, 1), "lbm": round(t_lbm, 1),
+                                            "train": round(t_train, 1)}},
+        "test": {"side": args.ws_test, "k_ref": ref["k"], "k_ref_steps": ref["steps"],
+                 "k_ref_converged": ref["converged"], **res}}}
+    print(json.dumps(out), flush=True)
+    net.close()
+
+
 def run_profile_case(args):
     """Small, fixed launch sequence for ncu: create the benchmark lattice, W
     single-step warm-up launches, then `steps` steps with per-launch events."""
@@ -485,6 +534,13 @@ def main(argv=None):
                     help="also run the time-to-steady-flux comparison (FP32 / FP16 / BF16)")
     ap.add_argument("--ensemble", action=argparse.BooleanOptionalAction, default=True,
                     help="also time the batched 64-member ensemble (FP16 deviation storage)")
+    ap.add_argument("--warmstart", action="store_true",
+                    help="run the learned warm-start experiment instead of the benchmark")
+    ap.add_argument("--ws-samples", type=int, default=512)
+    ap.add_argument("--ws-lbm-steps", type=int, default=8000)
+    ap.add_argument("--ws-epochs", type=int, default=30)
+    ap.add_argument("--ws-test", type=int, default=256)
+    ap.add_argument("--ws-ref-steps", type=int, default=300000)
     ap.add_argument("--profile-case", action="store_true",
                     help="run the short fixed launch sequence used for ncu captures")
     args = ap.parse_args(argv)
@@ -493,6 +549,8 @@ def main(argv=None):
     rank, world, local = dist_env()
     if args.profile_case:
         run_profile_case(args)
+    elif args.warmstart:
+        run_warmstart(args)
     elif args.impl == "reference":
         run_reference(args, rank, world, local)
     else:

@@ -202,6 +202,8 @@ int lbm_batch_get_flux(lbm_batch* b, int member, int face, double* Q, double* rh
 /* One member's distributions to/from a host array of 19*nx*ny*nz doubles [q][z][y][x]. */
 int lbm_batch_get_distributions(lbm_batch* b, int member, double* f);
 int lbm_batch_set_distributions(lbm_batch* b, int member, const double* f);
+/* One member's rho and u (as lbm_get_fields) into host arrays of nx*ny*nz doubles. */
+int lbm_batch_get_fields(lbm_batch* b, int member, double* rho, double* ux, double* uy, double* uz);
 /* Total pore nodes, 256-node tiles of the launch, steps taken.  NULLs allowed. */
 int lbm_batch_get_info(const lbm_batch* b, int64_t* n_pore, int64_t* n_tiles, int64_t* steps);
 /* Profiling aid: n >= 1 single-step launches with CUDA events around each on the
@@ -214,6 +216,42 @@ const char* lbm_batch_last_error(const lbm_batch* b);
  * ctx is NULL).  The string is owned by the library and valid until the next
  * call on the same context. */
 const char* lbm_last_error(const lbm_ctx* ctx);
+
+/* ---------------------------------------------------------------------------
+ * Learned warm start (not in the paper; a library addition).  A small 3-D
+ * U-Net (3 resolution levels with c0, c1, c2 channels, each in {8, 16, 32};
+ * 3x3x3 convolutions, ReLU, 2x2x2 mean pooling, nearest upsampling, additive
+ * skips) maps a voxel geometry to the steady velocity field divided by the
+ * superficial velocity u_D = Q / (nx ny).  Forward, backward (data and weight
+ * gradients) and Adam run in this library's CUDA kernels (FP32).  All volumes
+ * have sides divisible by 4; masks are uint8 [z][y][x], 1 = solid (as for
+ * lbm_create); fields are float32 [c][z][y][x] with c = u_x, u_y, u_z.
+ * Parameters are stored layer by layer as W[cout][cin][27] (taps dz, dy, dx
+ * each in -1, 0, 1) followed by b[cout]; they start at 0 until set.
+ * ------------------------------------------------------------------------- */
+typedef struct lbm_wsnet lbm_wsnet; /* opaque */
+int lbm_wsnet_create(int c0, int c1, int c2, lbm_wsnet** out);
+int lbm_wsnet_num_params(const lbm_wsnet* net, int64_t* n);
+int lbm_wsnet_set_stream(lbm_wsnet* net, void* cuda_stream);
+int lbm_wsnet_set_params(lbm_wsnet* net, const float* params);   /* host, num_params floats; resets Adam */
+int lbm_wsnet_get_params(lbm_wsnet* net, float* params);         /* host, num_params floats */
+/* Masked mean squared error over pore voxels of `batch` samples (host arrays:
+ * masks batch*nz*ny*nx bytes, targets batch*3*nz*ny*nx floats) and its gradient
+ * w.r.t. the parameters (host, num_params floats; may be NULL). */
+int lbm_wsnet_loss_grad(lbm_wsnet* net, const uint8_t* masks, const float* targets, int batch, int nx, int ny,
+                        int nz, double* loss, float* grad);
+/* Adam training (beta 0.9 / 0.999, eps 1e-8): `epochs` passes over n_samples
+ * host samples in mini-batches of `batch`, visiting samples in the caller's
+ * order (epochs*n_samples indices); mean loss per epoch into loss_history
+ * (epochs floats, may be NULL).  Synchronises. */
+int lbm_wsnet_train(lbm_wsnet* net, const uint8_t* masks, const float* targets, int n_samples, int nx, int ny,
+                    int nz, int epochs, int batch, float lr, const int* order, float* loss_history);
+/* Predicted u / u_D (host, 3*nz*ny*nx floats) of one geometry; 0 at solids. */
+int lbm_wsnet_predict(lbm_wsnet* net, const uint8_t* mask, int nx, int ny, int nz, float* y);
+/* Free the activation buffers kept between calls (they grow to the largest volume seen). */
+int lbm_wsnet_release_buffers(lbm_wsnet* net);
+int lbm_wsnet_destroy(lbm_wsnet* net);
+const char* lbm_wsnet_last_error(const lbm_wsnet* net);
 
 #ifdef __cplusplus
 }

@@ -319,6 +319,32 @@ __global__ void k_batch_decode(const typename S::T* __restrict__ f, int64_t ns, 
     });
 }
 
+// rho and u = j of one member's stored state into dense [z][y][x] arrays
+// (pre-zeroed), via the member's unpadded voxel index list.
+template <class S>
+__global__ void k_batch_export(const typename S::T* __restrict__ f, int64_t ns, const uint32_t* __restrict__ vox,
+                               const Member* members, int mi, const int64_t* __restrict__ unpadded, double* rho,
+                               double* ux, double* uy, double* uz) {
+    using M = typename S::M;
+    const Member& m = members[mi];
+    const int64_t il = (int64_t)blockIdx.x * kTile + threadIdx.x;
+    if (il >= m.n) return;
+    const int64_t i = m.base + il;
+    const M r_own = member_ref<S>(m, vox[i]);
+    M d[19];
+    for_q(AllQ{}, [&](auto qc) {
+        constexpr int Q = decltype(qc)::value;
+        d[Q] = S::template dec<Q>(f[(int64_t)Q * ns + i], r_own);
+    });
+    M drho, jx, jy, jz;
+    moments(d, drho, jx, jy, jz);
+    const int64_t o = unpadded[il];
+    rho[o] = 1.0 + (double)drho;
+    ux[o] = (double)jx;
+    uy[o] = (double)jy;
+    uz[o] = (double)jz;
+}
+
 template <class F>
 cudaError_t dispatch(int prec, F&& f) {
     switch (prec) {
@@ -782,6 +808,39 @@ int lbm_batch_set_distributions(lbm_batch* b, int member, const double* f) {
     cudaFree(d);
     if (e != cudaSuccess) return bfail(b, LBM_ECUDA, "lbm_batch_set_distributions: %s", cudaGetErrorString(e));
     return bprime(b);
+}
+
+int lbm_batch_get_fields(lbm_batch* b, int member, double* rho, double* ux, double* uy, double* uz) {
+    int rc = benter(b);
+    if (rc) return rc;
+    if (member < 0 || member >= b->nm) return bfail(b, LBM_EINVAL, "member %d out of range", member);
+    const lbm::Member& m = b->h_members[(size_t)member];
+    const size_t ncell = (size_t)b->dims[3 * member] * b->dims[3 * member + 1] * b->dims[3 * member + 2];
+    const auto& pv = b->pore_voxel[(size_t)member];
+    double* d = nullptr;
+    int64_t* dv = nullptr;
+    BATCH_CUDA(b, cudaMalloc(&d, 4 * ncell * sizeof(double)));
+    cudaError_t e = cudaMalloc(&dv, pv.size() * sizeof(int64_t));
+    if (e == cudaSuccess) e = cudaMemsetAsync(d, 0, 4 * ncell * sizeof(double), b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(dv, pv.data(), pv.size() * sizeof(int64_t), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess)
+        e = lbm::dispatch(b->prec, [&](auto s) {
+            using S = decltype(s);
+            lbm::k_batch_export<S><<<(unsigned)((m.n + lbm::kTile - 1) / lbm::kTile), lbm::kTile, 0, b->stream>>>(
+                (const typename S::T*)b->f[b->cur], b->ns, b->d_vox, b->d_members, member, dv, d, d + ncell,
+                d + 2 * ncell, d + 3 * ncell);
+            return cudaGetLastError();
+        });
+    double* outs[4] = {rho, ux, uy, uz};
+    for (int k = 0; k < 4 && e == cudaSuccess; ++k)
+        if (outs[k])
+            e = cudaMemcpyAsync(outs[k], d + k * ncell, ncell * sizeof(double), cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    cudaFree(d);
+    cudaFree(dv);
+    if (e != cudaSuccess) return bfail(b, LBM_ECUDA, "lbm_batch_get_fields: %s", cudaGetErrorString(e));
+    return LBM_OK;
 }
 
 int lbm_batch_get_info(const lbm_batch* b, int64_t* n_pore, int64_t* n_tiles, int64_t* steps) {

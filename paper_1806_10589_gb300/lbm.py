@@ -61,10 +61,24 @@ SIGNATURES = {
     "lbm_batch_get_flux": (C.c_int, [_P, C.c_int, C.c_int, _DP, _DP]),
     "lbm_batch_get_distributions": (C.c_int, [_P, C.c_int, _DP]),
     "lbm_batch_set_distributions": (C.c_int, [_P, C.c_int, _DP]),
+    "lbm_batch_get_fields": (C.c_int, [_P, C.c_int, _DP, _DP, _DP, _DP]),
     "lbm_batch_get_info": (C.c_int, [_P, _I64P, _I64P, _I64P]),
     "lbm_batch_time_step": (C.c_int, [_P, C.c_int, _FP]),
     "lbm_batch_destroy": (C.c_int, [_P]),
     "lbm_batch_last_error": (C.c_char_p, [_P]),
+    "lbm_wsnet_create": (C.c_int, [C.c_int, C.c_int, C.c_int, C.POINTER(_P)]),
+    "lbm_wsnet_num_params": (C.c_int, [_P, _I64P]),
+    "lbm_wsnet_set_stream": (C.c_int, [_P, _P]),
+    "lbm_wsnet_set_params": (C.c_int, [_P, _FP]),
+    "lbm_wsnet_get_params": (C.c_int, [_P, _FP]),
+    "lbm_wsnet_loss_grad": (C.c_int, [_P, C.POINTER(C.c_uint8), _FP, C.c_int, C.c_int, C.c_int, C.c_int, _DP,
+                                      _FP]),
+    "lbm_wsnet_train": (C.c_int, [_P, C.POINTER(C.c_uint8), _FP, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                                  C.c_int, C.c_float, C.POINTER(C.c_int), _FP]),
+    "lbm_wsnet_predict": (C.c_int, [_P, C.POINTER(C.c_uint8), C.c_int, C.c_int, C.c_int, _FP]),
+    "lbm_wsnet_release_buffers": (C.c_int, [_P]),
+    "lbm_wsnet_destroy": (C.c_int, [_P]),
+    "lbm_wsnet_last_error": (C.c_char_p, [_P]),
 }
 
 _lib = None
@@ -307,6 +321,12 @@ class Batch:
             raise ValueError("f must have shape (19,) + mask.shape")
         self._check(self._lib.lbm_batch_set_distributions(self._h, int(member), _ptr(f, C.c_double)))
 
+    def fields(self, member):
+        shape = self._masks[member].shape
+        arrs = [np.empty(shape) for _ in range(4)]
+        self._check(self._lib.lbm_batch_get_fields(self._h, int(member), *[_ptr(a, C.c_double) for a in arrs]))
+        return tuple(arrs)
+
     def info(self):
         v = [C.c_int64() for _ in range(3)]
         self._check(self._lib.lbm_batch_get_info(self._h, *[C.byref(x) for x in v]))
@@ -316,3 +336,85 @@ class Batch:
         ms = C.c_float()
         self._check(self._lib.lbm_batch_time_step(self._h, int(n), C.byref(ms)))
         return ms.value
+
+
+class WarmStartNet:
+    """The warm-start network (lbm_wsnet_*)."""
+
+    def __init__(self, c0=8, c1=16, c2=32, stream=None):
+        lib = load_library()
+        h = _P()
+        st = lib.lbm_wsnet_create(int(c0), int(c1), int(c2), C.byref(h))
+        if st != LBM_OK:
+            raise LBMError(st, "lbm_wsnet_create(%d, %d, %d)" % (c0, c1, c2))
+        self._h, self._lib, self.chans = h, lib, (c0, c1, c2)
+        n = C.c_int64()
+        self._check(lib.lbm_wsnet_num_params(h, C.byref(n)))
+        self.n_params = n.value
+        if stream is not None:
+            hs = getattr(stream, "cuda_stream", stream)
+            self._check(lib.lbm_wsnet_set_stream(h, _P(hs) if hs else None))
+
+    def _check(self, st):
+        if st != LBM_OK:
+            raise LBMError(st, self._lib.lbm_wsnet_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.lbm_wsnet_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def layer_shapes(self):
+        """(cout, cin) of the 11 convolutions in the library's parameter order."""
+        c0, c1, c2 = self.chans
+        return [(c0, 1), (c0, c0), (c1, c0), (c1, c1), (c2, c1), (c2, c2), (c1, c2), (c1, c1), (c0, c1),
+                (c0, c0), (3, c0)]
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        if p.size != self.n_params:
+            raise ValueError("expected %d parameters" % self.n_params)
+        self._check(self._lib.lbm_wsnet_set_params(self._h, _ptr(p, C.c_float)))
+
+    def params(self):
+        p = np.empty(self.n_params, np.float32)
+        self._check(self._lib.lbm_wsnet_get_params(self._h, _ptr(p, C.c_float)))
+        return p
+
+    def loss_grad(self, masks, targets):
+        masks = np.ascontiguousarray(masks, dtype=np.uint8)
+        targets = np.ascontiguousarray(targets, dtype=np.float32)
+        B, nz, ny, nx = masks.shape
+        loss = C.c_double()
+        g = np.empty(self.n_params, np.float32)
+        self._check(self._lib.lbm_wsnet_loss_grad(self._h, _ptr(masks, C.c_uint8), _ptr(targets, C.c_float), B,
+                                                  nx, ny, nz, C.byref(loss), _ptr(g, C.c_float)))
+        return loss.value, g
+
+    def train(self, masks, targets, epochs, batch, lr, seed=0):
+        masks = np.ascontiguousarray(masks, dtype=np.uint8)
+        targets = np.ascontiguousarray(targets, dtype=np.float32)
+        S, nz, ny, nx = masks.shape
+        rng = np.random.default_rng(seed)
+        order = np.ascontiguousarray(np.concatenate([rng.permutation(S) for _ in range(epochs)]).astype(np.int32))
+        hist = np.empty(epochs, np.float32)
+        self._check(self._lib.lbm_wsnet_train(self._h, _ptr(masks, C.c_uint8), _ptr(targets, C.c_float), S, nx, ny,
+                                              nz, int(epochs), int(batch), float(lr), _ptr(order, C.c_int),
+                                              _ptr(hist, C.c_float)))
+        return hist
+
+    def predict(self, mask):
+        mask = np.ascontiguousarray(mask, dtype=np.uint8)
+        nz, ny, nx = mask.shape
+        y = np.empty((3, nz, ny, nx), np.float32)
+        self._check(self._lib.lbm_wsnet_predict(self._h, _ptr(mask, C.c_uint8), nx, ny, nz, _ptr(y, C.c_float)))
+        return y
+
+    def release_buffers(self):
+        self._check(self._lib.lbm_wsnet_release_buffers(self._h))
