@@ -153,7 +153,10 @@ __device__ __forceinline__ M warp_sum_m(M v) {
 template <class M>
 __device__ __forceinline__ M warp_max_m(M v) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = v > __shfl_down_sync(0xffffffffu, v, o) ? v : __shfl_down_sync(0xffffffffu, v, o);
+    for (int o = 16; o > 0; o >>= 1) {
+        const M w = __shfl_down_sync(0xffffffffu, v, o);  // every lane shuffles, then compares
+        v = v > w ? v : w;
+    }
     return v;
 }
 template <int NT, class M>
