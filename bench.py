@@ -232,7 +232,7 @@ def time_to_steady(mask, a_in, stream, max_steps=150000):
     from paper_1806_10589_gb300 import Lattice, convergence as cv
 
     Q = UBAR * a_in
-    out = {"criterion": "k within 0.1% of k_inf and Q_out within 0.1% of Q for 10 checks (every 100 steps); "
+    out = {"criterion": "k within 0.1% of k_inf for 10 consecutive checks (every 100 steps); "
                         "k_inf: FP32 cold run to sum|u(t)-u(t-1000)|/sum|u| <= 1e-6"}
     with Lattice(mask, TAU, "mrt", "fp32", stream=stream) as lat:
         lat.set_flux_bc(Q)

@@ -4,8 +4,11 @@ on the state happens here; every number comes from the library's kernels).
 Two stopping rules:
   * Section 3.1 (Eq. stopping_criterion): sum|u(t) - u(t - lag)| / sum|u(t)| <= tol,
     lag = 1000 steps, tol = 1e-6 (lbm_steady_residual);
-  * 0.1 % rule: the permeability k(t) is within rtol of a reference k_inf and the
-    outlet flux within rtol of the prescribed Q, for `hold` consecutive checks.
+  * 0.1 % rule: the permeability k(t) is within rtol of a reference k_inf for
+    `hold` consecutive checks (optionally also the outlet flux within rtol of Q).
+    The outlet-plane sum of u_z is not the discrete mass flux across the outlet:
+    warm-started runs reach the reference k (to 1e-8) and a constant total mass
+    while that sum can stay ~1 % from Q, so it is reported, not required.
 
 k(t) = nu * u_D * (nz - 1) / dp  (Darcy's law; the paper does not define it),
 with nu = (tau - 1/2)/3 (Appendix A), u_D = Q / (nx ny) the superficial velocity
@@ -56,10 +59,11 @@ def run_to_residual(lat, Q, tau, lag=1000, tol=1e-6, max_steps=400000, sync=None
 
 
 def run_to_reference(lat, Q, tau, k_ref, rtol=1e-3, hold=10, check_every=100, max_steps=400000,
-                     sync=None):
-    """Step until k(t) and the outlet flux stay within rtol of k_ref and Q for
-    `hold` consecutive checks.  t_steady is the first check of that run of
-    checks.  Returns dict(steps, seconds, k, q_out, reached)."""
+                     sync=None, require_q_out=False):
+    """Step until k(t) stays within rtol of k_ref (and, if require_q_out, the
+    outlet flux within rtol of Q) for `hold` consecutive checks.  t_steady is
+    the first check of that run of checks.  Returns dict(steps, seconds, k,
+    q_out, reached)."""
     t0 = time.perf_counter()
     steps = 0
     streak = 0
@@ -69,7 +73,9 @@ def run_to_reference(lat, Q, tau, k_ref, rtol=1e-3, hold=10, check_every=100, ma
         lat.step(check_every)
         steps += check_every
         s = sample(lat, Q, tau)
-        ok = abs(s["k"] - k_ref) <= rtol * abs(k_ref) and abs(s["q_out"] - Q) <= rtol * abs(Q)
+        ok = abs(s["k"] - k_ref) <= rtol * abs(k_ref)
+        if require_q_out:
+            ok = ok and abs(s["q_out"] - Q) <= rtol * abs(Q)
         if ok:
             if streak == 0:
                 first, first_t = steps, time.perf_counter() - t0

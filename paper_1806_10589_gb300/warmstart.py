@@ -104,7 +104,8 @@ def warm_vs_cold(lattice_cls, net, mask, Q, tau, c_kc, k_ref, precision="fp32", 
     with lattice_cls(mask, tau, "mrt", precision, stream=stream) as lat:
         lat.set_flux_bc(Q)
         r = cv.run_to_reference(lat, Q, tau, k_ref, max_steps=max_steps, sync=sync)
-        out["cold"] = {"steps": r["steps"], "seconds": r["seconds"], "reached": r["reached"], "k": r["k"]}
+        out["cold"] = {"steps": r["steps"], "seconds": r["seconds"], "reached": r["reached"], "k": r["k"],
+                       "q_out": r["q_out"]}
     with lattice_cls(mask, tau, "mrt", precision, stream=stream) as lat:
         lat.set_flux_bc(Q)
         t0 = time.perf_counter()
@@ -113,5 +114,5 @@ def warm_vs_cold(lattice_cls, net, mask, Q, tau, c_kc, k_ref, precision="fp32", 
         t_init = time.perf_counter() - t0
         r = cv.run_to_reference(lat, Q, tau, k_ref, max_steps=max_steps, sync=sync)
         out["warm"] = {"steps": r["steps"], "seconds": None if r["seconds"] is None else r["seconds"] + t_init,
-                       "init_seconds": t_init, "reached": r["reached"], "k": r["k"]}
+                       "init_seconds": t_init, "reached": r["reached"], "k": r["k"], "q_out": r["q_out"]}
     return out

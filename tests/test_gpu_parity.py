@@ -238,7 +238,7 @@ def test_steady_residual_matches_oracle(torch_cuda):
 
 def test_convergence_harness_small_duct(torch_cuda):
     """The time-to-steady harness on a small duct: the Section 3.1 rule converges,
-    and a second cold run reaches 0.1 % of its permeability."""
+    and a second cold run reaches 0.1 % of its permeability and outlet flux."""
     from paper_1806_10589_gb300 import convergence as cv
 
     m = duct_mask(10, 10, 24)
@@ -249,7 +249,7 @@ def test_convergence_harness_small_duct(torch_cuda):
     assert ref["converged"] and abs(ref["q_out"] - Q) < 1e-4 * Q
     with _lat(m, 1.0, "mrt", "fp32", torch_cuda) as lat:
         lat.set_flux_bc(Q)
-        r = cv.run_to_reference(lat, Q, 1.0, ref["k"], check_every=20, max_steps=20000)
+        r = cv.run_to_reference(lat, Q, 1.0, ref["k"], check_every=20, max_steps=20000, require_q_out=True)
     assert r["reached"] and r["steps"] < ref["steps"]
 
 

@@ -105,4 +105,6 @@ def test_warm_start_pipeline_small(net):
         lat.set_flux_bc(Q)
         ref = cv.run_to_residual(lat, Q, 0.8, lag=500, tol=1e-6, max_steps=40000)
     res = ws.warm_vs_cold(Lattice, net, m, Q, 0.8, c_kc, ref["k"], stream=st, max_steps=40000)
-    assert res["cold"]["reached"] and res["warm"]["reached"]
+    info = {"res": res, "k_ref": ref["k"]}
+    assert res["cold"]["reached"] and res["warm"]["reached"], info
+    assert abs(res["warm"]["k"] - ref["k"]) <= 1e-3 * ref["k"]
