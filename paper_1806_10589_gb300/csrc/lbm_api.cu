@@ -26,7 +26,7 @@ namespace {
 
 constexpr int kGraphSteps = 64;  // steps per captured graph (even: parity preserved)
 #ifndef LBM_DEFAULT_STEP_VARIANT
-#define LBM_DEFAULT_STEP_VARIANT 1
+#define LBM_DEFAULT_STEP_VARIANT 0
 #endif
 constexpr int kDefaultStepVariant = LBM_DEFAULT_STEP_VARIANT;
 constexpr int64_t kReencodeInterval = 1024;  // steps between 16-bit reference refreshes

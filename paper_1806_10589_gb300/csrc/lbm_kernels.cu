@@ -104,7 +104,7 @@ __device__ __forceinline__ void st_stream(T* a, T v, uint64_t pol) {
 // bounce-back; the z-outside ones are replaced by the closure).
 template <class S>
 __device__ __forceinline__ void pull_step(typename S::M* d, const StepPtrs<typename S::T>& P,
-                                          const DevLattice& L, int64_t p, int i, uint64_t pol_f,
+                                          const DevLattice& L, uint32_t p, int i, uint64_t pol_f,
                                           uint64_t pol_idx, typename S::M r_own, typename S::M g) {
     using M = typename S::M;
     for_q(AllQ{}, [&](auto qc) {
@@ -112,7 +112,8 @@ __device__ __forceinline__ void pull_step(typename S::M* d, const StepPtrs<typen
         if constexpr (Q == 0) {
             d[0] = S::template dec<0>(ld_stream(P.in[0] + i, pol_f), r_own);
         } else {
-            const int id = ld_index(L.grid + p + L.goff[Q], pol_idx);
+            // padded voxel indices fit in 32 bits (checked at creation)
+            const int id = ld_index(L.grid + (uint32_t)(p + (uint32_t)L.goff[Q]), pol_idx);
             const typename S::T* a = id >= 0 ? P.in[Q] + id : P.in[opp(Q)] + i;
             // a pulled value was written on plane z - xi_z (reference r_own - g xi_z)
             const M r = (cz(Q) != 0 && id >= 0) ? r_own - M(cz(Q)) * g : r_own;
@@ -274,8 +275,8 @@ k_inlet_reduce(const typename S::T* __restrict__ fin, int slot, DevLattice L, Bc
 //   z = 1:  twice each xi_z = -1 value whose destination on z = 0 is a pore.
 // Values are taken as the next step will decode them from storage.
 template <class S>
-__device__ __forceinline__ double next_inlet_part(const typename S::M* d, const DevLattice& L,
-                                                  int64_t p, int i, typename S::M r_own) {
+__device__ __noinline__ double next_inlet_part(const typename S::M* d, const DevLattice& L,
+                                               int64_t p, int i, typename S::M r_own) {
     double s = 0.0;
     auto val = [&](auto qc) -> double {
         constexpr int Q = decltype(qc)::value;
@@ -318,7 +319,7 @@ k_step(const StepPtrs<typename S::T> P, int slot, DevLattice L, typename S::M sp
 #else
         const uint64_t pol_idx = 0;
 #endif
-        const int64_t p = ld_index(L.vox + i, pol_idx);
+        const uint32_t p = ld_index(L.vox + i, pol_idx);
         const M r_own = own_ref<S>(bc, L, p), g = own_slope<S>(bc);
         M d[19];
         pull_step<S>(d, P, L, p, i, pol_f, pol_idx, r_own, g);
