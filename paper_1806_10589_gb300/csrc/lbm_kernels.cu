@@ -27,7 +27,7 @@ constexpr int kReduceBlock = 256;
 // Resident 256-thread blocks per SM the step kernel is compiled for (caps its
 // registers at 65536 / (256 * n)); FP64 arithmetic is left unconstrained.
 #ifndef LBM_STEP_MIN_BLOCKS
-#define LBM_STEP_MIN_BLOCKS 4
+#define LBM_STEP_MIN_BLOCKS 5
 #endif
 template <class S>
 constexpr int step_min_blocks() {
@@ -64,6 +64,12 @@ struct StepPtrs {
     const T* in[19];
     T* out[19];
 };
+
+// LBM_CONTRIB_RELOAD: the per-node kernel forms the next step's inlet
+// contribution from reloaded stored values (1) or from the registers (0).
+#ifndef LBM_CONTRIB_RELOAD
+#define LBM_CONTRIB_RELOAD 1
+#endif
 
 // LBM_L2_HINTS: 0 = no hints; 1 = index structures evict-last; 2 = also the
 // distribution streams evict-first.
@@ -273,18 +279,14 @@ k_inlet_reduce(const typename S::T* __restrict__ fin, int slot, DevLattice L, Bc
 //   z = 0:  all xi_z = 0 values (they stay on the plane either way), plus twice
 //           each xi_z = +1 value whose destination on z = 1 is solid;
 //   z = 1:  twice each xi_z = -1 value whose destination on z = 0 is a pore.
-// Values are taken as the next step will decode them from storage.
-template <class S>
-__device__ __noinline__ double next_inlet_part(const typename S::M* d, const DevLattice& L,
-                                               int64_t p, int i, typename S::M r_own) {
+// `val(Q)` returns the stored value of direction Q exactly as the next step
+// will decode it.
+template <class S, class V>
+__device__ __forceinline__ double inlet_contribution(const DevLattice& L, uint32_t p, int i, V&& val) {
     double s = 0.0;
-    auto val = [&](auto qc) -> double {
-        constexpr int Q = decltype(qc)::value;
-        return (double)S::template dec<Q>(S::template enc<Q>(d[Q], r_own), r_own);
-    };
     auto dest_is_pore = [&](auto qc) -> bool {
         constexpr int Q = decltype(qc)::value;  // destination i + xi_Q = pull source of opp(Q)
-        return __ldg(L.grid + p + L.goff[opp(Q)]) >= 0;
+        return __ldg(L.grid + (uint32_t)(p + (uint32_t)L.goff[opp(Q)])) >= 0;
     };
     if (i < L.a_in) {
         for_q(std::integer_sequence<int, 0, 1, 2, 3, 4, 7, 8, 9, 10>{},
@@ -296,6 +298,29 @@ __device__ __noinline__ double next_inlet_part(const typename S::M* d, const Dev
               [&](auto qc) { if (dest_is_pore(qc)) s += 2.0 * val(qc); });
     }
     return s;
+}
+
+// From values still in registers (the pipelined kernel).
+template <class S>
+__device__ __forceinline__ double next_inlet_part(const typename S::M* d, const DevLattice& L,
+                                                  int64_t p, int i, typename S::M r_own) {
+    return inlet_contribution<S>(L, (uint32_t)p, i, [&](auto qc) -> double {
+        constexpr int Q = decltype(qc)::value;
+        return (double)S::template dec<Q>(S::template enc<Q>(d[Q], r_own), r_own);
+    });
+}
+
+// From the values this thread has just stored (the per-node kernel): the
+// registers of the collision are free again, and only the ~2 % of nodes on the
+// planes next to the inlet pay the reload.
+template <class S>
+__device__ __forceinline__ double next_inlet_part_stored(const StepPtrs<typename S::T>& P, const DevLattice& L,
+                                                         uint32_t p, int i, typename S::M r_own) {
+    return inlet_contribution<S>(L, p, i, [&](auto qc) -> double {
+        constexpr int Q = decltype(qc)::value;
+        const typename S::T v = *(volatile const typename S::T*)(P.out[Q] + i);
+        return (double)S::template dec<Q>(v, r_own);
+    });
 }
 
 template <class S>
@@ -334,7 +359,11 @@ k_step(const StepPtrs<typename S::T> P, int slot, DevLattice L, typename S::M sp
         }
         collide(d, sp, sm);
         store_step<S>(d, P, i, pol_f, r_own);
+#if LBM_CONTRIB_RELOAD
+        if (i64 < L.a_01) part = next_inlet_part_stored<S>(P, L, p, i, r_own);
+#else
         if (i64 < L.a_01) part = next_inlet_part<S>(d, L, p, i, r_own);
+#endif
     }
     // blocks that hold plane z = 0 or z = 1 nodes (block-uniform branch)
     if ((int64_t)blockIdx.x * kBlock < L.a_01) {
