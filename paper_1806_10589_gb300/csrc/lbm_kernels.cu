@@ -27,7 +27,7 @@ constexpr int kReduceBlock = 256;
 // Resident 256-thread blocks per SM the step kernel is compiled for (caps its
 // registers at 65536 / (256 * n)); FP64 arithmetic is left unconstrained.
 #ifndef LBM_STEP_MIN_BLOCKS
-#define LBM_STEP_MIN_BLOCKS 5
+#define LBM_STEP_MIN_BLOCKS 4
 #endif
 template <class S>
 constexpr int step_min_blocks() {
@@ -65,11 +65,18 @@ struct StepPtrs {
     T* out[19];
 };
 
-// LBM_CONTRIB_RELOAD: the per-node kernel forms the next step's inlet
-// contribution from reloaded stored values (1) or from the registers (0).
-#ifndef LBM_CONTRIB_RELOAD
-#define LBM_CONTRIB_RELOAD 1
+// The per-node kernel forms the next step's inlet contribution from the
+// registers (FP32/FP64: measured faster) or by reloading the values it has just
+// stored (16-bit formats: frees the decode state, measured faster).
+// LBM_CONTRIB_RELOAD = 0 / 1 forces one way for every format.
+template <class S>
+constexpr bool contrib_reload() {
+#ifdef LBM_CONTRIB_RELOAD
+    return LBM_CONTRIB_RELOAD != 0;
+#else
+    return S::kRef;
 #endif
+}
 
 // LBM_L2_HINTS: 0 = no hints; 1 = index structures evict-last; 2 = also the
 // distribution streams evict-first.
@@ -359,11 +366,10 @@ k_step(const StepPtrs<typename S::T> P, int slot, DevLattice L, typename S::M sp
         }
         collide(d, sp, sm);
         store_step<S>(d, P, i, pol_f, r_own);
-#if LBM_CONTRIB_RELOAD
-        if (i64 < L.a_01) part = next_inlet_part_stored<S>(P, L, p, i, r_own);
-#else
-        if (i64 < L.a_01) part = next_inlet_part<S>(d, L, p, i, r_own);
-#endif
+        if (i64 < L.a_01) {
+            if constexpr (contrib_reload<S>()) part = next_inlet_part_stored<S>(P, L, p, i, r_own);
+            else part = next_inlet_part<S>(d, L, p, i, r_own);
+        }
     }
     // blocks that hold plane z = 0 or z = 1 nodes (block-uniform branch)
     if ((int64_t)blockIdx.x * kBlock < L.a_01) {
