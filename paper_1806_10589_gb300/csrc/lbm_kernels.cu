@@ -70,7 +70,7 @@ struct StepPtrs {
 // stored (16-bit formats: frees the decode state, measured faster).
 // LBM_CONTRIB_RELOAD = 0 / 1 forces one way for every format.
 template <class S>
-constexpr bool contrib_reload() {
+__host__ __device__ constexpr bool contrib_reload() {
 #ifdef LBM_CONTRIB_RELOAD
     return LBM_CONTRIB_RELOAD != 0;
 #else
