@@ -218,6 +218,38 @@ const char* lbm_batch_last_error(const lbm_batch* b);
 const char* lbm_last_error(const lbm_ctx* ctx);
 
 /* ---------------------------------------------------------------------------
+ * Two-fluid colour model (Appendix A) with the flux inlet of Section 2.
+ * Momentum: D3Q19 as above, with the interfacial equilibrium terms
+ * m1 += alpha|C|, m9 += alpha|C|/2 (2nx^2 - ny^2 - nz^2), m11 += alpha|C|/2 (ny^2 - nz^2),
+ * m13/m14/m15 += alpha|C|/2 nx ny / ny nz / nx nz, C = grad phi, n = C/|C|.
+ * Phases: D3Q7 A and B (w0 = 1/3, w1..6 = 1/9) with the recolouring update
+ * A_q(x + xi_q) = w_q N_A [1 + 9/2 u.xi_q + beta N_B n.xi_q] (B with -beta N_A),
+ * phi = (N_A - N_B)/(N_A + N_B).  Readings of the silent points: C is the
+ * isotropic D3Q19 stencil 3 sum_q w_q xi_q phi(x + xi_q), a solid neighbour
+ * contributes phi_s (wetting: +1 = the solid looks like phase A), a z-outside
+ * neighbour the node's own phi; the inlet injects phase fraction phi_in, the
+ * outlet lets both phases leave with their local composition.  FP64 or FP32
+ * storage.  A mask whose z = 0 (z = nz-1) plane is all solid has no inlet
+ * (outlet) condition, so closed boxes are allowed.
+ * ------------------------------------------------------------------------- */
+typedef struct lbm_color lbm_color; /* opaque */
+int lbm_color_create(const uint8_t* mask, int nx, int ny, int nz, double tau, double alpha, double beta,
+                     double phi_s, int precision, lbm_color** out);
+int lbm_color_set_stream(lbm_color* c, void* cuda_stream);
+/* Inlet flux Q (Eq. flux, Eq. potential) and the phase phi_in of the injected fluid. */
+int lbm_color_set_flux_bc(lbm_color* c, double Q, double phi_in);
+/* Whole state from/to host arrays [q][z][y][x]: f 19, A 7 and B 7 planes of nx*ny*nz doubles. */
+int lbm_color_set_state(lbm_color* c, const double* f, const double* A, const double* B);
+int lbm_color_get_state(lbm_color* c, double* f, double* A, double* B);
+int lbm_color_step(lbm_color* c, int n);
+/* rho, u and phi of the current state (host, nx*ny*nz doubles each; NULLs allowed; 0 at solids). */
+int lbm_color_get_fields(lbm_color* c, double* rho, double* ux, double* uy, double* uz, double* phi);
+/* Sum of u_z over the inlet or outlet pore nodes, and the face density. */
+int lbm_color_get_flux(lbm_color* c, int face, double* Q, double* rho_bc);
+int lbm_color_destroy(lbm_color* c);
+const char* lbm_color_last_error(const lbm_color* c);
+
+/* ---------------------------------------------------------------------------
  * Learned warm start (not in the paper; a library addition).  A small 3-D
  * U-Net (3 resolution levels with c0, c1, c2 channels, each in {8, 16, 32};
  * 3x3x3 convolutions, ReLU, 2x2x2 mean pooling, nearest upsampling, additive

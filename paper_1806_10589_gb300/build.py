@@ -19,7 +19,7 @@ LIB_NAME = "libgb300lbm.so"
 LIB_PATH = os.path.join(PKG, LIB_NAME)
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
-SOURCES = ["lbm_kernels.cu", "lbm_api.cu", "lbm_noalloc.cu", "lbm_batch.cu", "wsnet.cu"]
+SOURCES = ["lbm_kernels.cu", "lbm_api.cu", "lbm_noalloc.cu", "lbm_batch.cu", "wsnet.cu", "lbm_color.cu"]
 
 
 def nvcc_path() -> str:

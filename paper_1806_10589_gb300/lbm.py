@@ -66,6 +66,17 @@ SIGNATURES = {
     "lbm_batch_time_step": (C.c_int, [_P, C.c_int, _FP]),
     "lbm_batch_destroy": (C.c_int, [_P]),
     "lbm_batch_last_error": (C.c_char_p, [_P]),
+    "lbm_color_create": (C.c_int, [C.POINTER(C.c_uint8), C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
+                                   C.c_double, C.c_double, C.c_int, C.POINTER(_P)]),
+    "lbm_color_set_stream": (C.c_int, [_P, _P]),
+    "lbm_color_set_flux_bc": (C.c_int, [_P, C.c_double, C.c_double]),
+    "lbm_color_set_state": (C.c_int, [_P, _DP, _DP, _DP]),
+    "lbm_color_get_state": (C.c_int, [_P, _DP, _DP, _DP]),
+    "lbm_color_step": (C.c_int, [_P, C.c_int]),
+    "lbm_color_get_fields": (C.c_int, [_P, _DP, _DP, _DP, _DP, _DP]),
+    "lbm_color_get_flux": (C.c_int, [_P, C.c_int, _DP, _DP]),
+    "lbm_color_destroy": (C.c_int, [_P]),
+    "lbm_color_last_error": (C.c_char_p, [_P]),
     "lbm_wsnet_create": (C.c_int, [C.c_int, C.c_int, C.c_int, C.POINTER(_P)]),
     "lbm_wsnet_num_params": (C.c_int, [_P, _I64P]),
     "lbm_wsnet_set_stream": (C.c_int, [_P, _P]),
@@ -418,3 +429,70 @@ class WarmStartNet:
 
     def release_buffers(self):
         self._check(self._lib.lbm_wsnet_release_buffers(self._h))
+
+
+class ColorLattice:
+    """Two-fluid colour model (lbm_color_*).  mask: uint8 [z][y][x], 1 = solid."""
+
+    def __init__(self, mask, tau, alpha, beta=0.95, phi_s=-1.0, precision="fp64", stream=None):
+        lib = load_library()
+        mask = np.ascontiguousarray(mask, dtype=np.uint8)
+        self.nz, self.ny, self.nx = mask.shape
+        self.shape = mask.shape
+        h = _P()
+        st = lib.lbm_color_create(_ptr(mask, C.c_uint8), self.nx, self.ny, self.nz, float(tau), float(alpha),
+                                  float(beta), float(phi_s), PRECISIONS[precision], C.byref(h))
+        if st != LBM_OK:
+            raise LBMError(st, lib.lbm_color_last_error(None).decode())
+        self._h, self._lib = h, lib
+        if stream is not None:
+            hs = getattr(stream, "cuda_stream", stream)
+            self._check(lib.lbm_color_set_stream(h, _P(hs) if hs else None))
+
+    def _check(self, st):
+        if st != LBM_OK:
+            raise LBMError(st, self._lib.lbm_color_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.lbm_color_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_flux_bc(self, Q, phi_in=1.0):
+        self._check(self._lib.lbm_color_set_flux_bc(self._h, float(Q), float(phi_in)))
+
+    def set_state(self, f, A, B):
+        cv = [np.ascontiguousarray(a, dtype=np.float64) for a in (f, A, B)]
+        self._check(self._lib.lbm_color_set_state(self._h, *[_ptr(a, C.c_double) for a in cv]))
+
+    def state(self):
+        f = np.empty((19,) + self.shape)
+        A = np.empty((7,) + self.shape)
+        B = np.empty((7,) + self.shape)
+        self._check(self._lib.lbm_color_get_state(self._h, *[_ptr(a, C.c_double) for a in (f, A, B)]))
+        return f, A, B
+
+    def step(self, n=1):
+        self._check(self._lib.lbm_color_step(self._h, int(n)))
+
+    def fields(self):
+        arrs = [np.empty(self.shape) for _ in range(5)]
+        self._check(self._lib.lbm_color_get_fields(self._h, *[_ptr(a, C.c_double) for a in arrs]))
+        return tuple(arrs)
+
+    def get_flux(self, face=LBM_FACE_ZMIN):
+        q, r = C.c_double(), C.c_double()
+        self._check(self._lib.lbm_color_get_flux(self._h, face, C.byref(q), C.byref(r)))
+        return q.value, r.value

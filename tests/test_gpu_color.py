@@ -1,0 +1,149 @@
+"""GPU parity of the two-fluid colour model (lbm_color_*) against the FP64 colour
+oracle, its single-phase limit against the single-fluid path, phase mass
+conservation in a closed box, and the Laplace law of a static droplet.
+
+Tolerances: FP64 1e-11 relative (as the single-fluid path); FP32 the same
+per-step budget as the single-fluid FP32 test (20 N eps32 of the largest
+deviation of each field)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import color_oracle as CO
+from lbm_inputs import duct_mask, random_mask, uniform_field
+
+pytestmark = pytest.mark.gpu
+EPS32 = float(np.finfo(np.float32).eps)
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+    import __graft_entry__
+
+    __graft_entry__.build()
+    return torch
+
+
+def _case(m, seed, phi_s, closed=False, Q=0.004):
+    ref = CO.ColourOracle(m, 0.8, alpha=0.01, beta=0.9, phi_s=phi_s, Q=Q, phi_in=1.0,
+                          inlet=None if closed else "flux", outlet=None if closed else "pressure")
+    phi0 = np.tanh(2.0 * uniform_field(m.shape, seed))
+    ref.init_phase(phi0, rho=1.0 + 0.01 * uniform_field(m.shape, seed + 1))
+    ref.f = ref.f * (1.0 + 0.01 * uniform_field(ref.f.shape, seed + 2))
+    ref.f[:, m == 1] = 0.0
+    return ref
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_colour_fp64_matches_oracle(torch_cuda, seed):
+    from paper_1806_10589_gb300 import ColorLattice
+
+    m = random_mask(9, 8, 12, 0.25, 40 + seed)
+    ref = _case(m, 50 + seed, -0.5)
+    f0, A0, B0 = ref.f.copy(), ref.A.copy(), ref.B.copy()
+    with ColorLattice(m, 0.8, 0.01, 0.9, -0.5, "fp64", stream=torch_cuda.cuda.current_stream()) as c:
+        c.set_flux_bc(0.004, 1.0)
+        c.set_state(f0, A0, B0)
+        c.step(15)
+        f, A, B = c.state()
+        q_in, rho_in = c.get_flux(4)
+    ref.step(15)
+    assert np.abs(f - ref.f).max() <= 1e-11 * np.abs(ref.f).max()
+    assert np.abs(A - ref.A).max() <= 1e-11 * np.abs(ref.A).max()
+    assert np.abs(B - ref.B).max() <= 1e-11 * np.abs(ref.B).max()
+    assert abs(rho_in - ref.rho_in) <= 1e-12
+    A_ = int((m[0] == 0).sum())
+    assert abs(q_in - 0.004) <= 8 * A_ * np.finfo(float).eps
+
+
+def test_colour_fp32_matches_oracle(torch_cuda):
+    from paper_1806_10589_gb300 import ColorLattice
+
+    m = random_mask(9, 8, 12, 0.25, 42)
+    ref = _case(m, 60, -0.5)
+    f0, A0, B0 = ref.f.copy(), ref.A.copy(), ref.B.copy()
+    N = 10
+    with ColorLattice(m, 0.8, 0.01, 0.9, -0.5, "fp32", stream=torch_cuda.cuda.current_stream()) as c:
+        c.set_flux_bc(0.004, 1.0)
+        c.set_state(f0, A0, B0)
+        c.step(N)
+        f, A, B = c.state()
+    ref.step(N)
+    d_ref = ref.f - O.W[:, None, None, None] * (m == 0)
+    assert np.abs(f - ref.f).max() <= 20 * N * EPS32 * np.abs(d_ref).max() + 4 * EPS32
+    assert np.abs(A - ref.A).max() <= 20 * N * EPS32 * np.abs(ref.A).max()
+    assert np.abs(B - ref.B).max() <= 20 * N * EPS32 * np.abs(ref.B).max()
+
+
+def test_colour_single_phase_limit_equals_single_fluid(torch_cuda):
+    from paper_1806_10589_gb300 import ColorLattice, Lattice
+
+    m = random_mask(10, 9, 12, 0.25, 7)
+    st = torch_cuda.cuda.current_stream()
+    with ColorLattice(m, 0.8, 0.01, 0.9, 1.0, "fp64", stream=st) as c, Lattice(m, 0.8, "mrt", "fp64", stream=st) as s:
+        ref = CO.ColourOracle(m, 0.8, alpha=0.01, beta=0.9, phi_s=1.0)
+        ref.init_phase(np.ones(m.shape))
+        c.set_state(ref.f, ref.A, ref.B)
+        c.set_flux_bc(0.003, 1.0)
+        s.set_flux_bc(0.003)
+        c.step(30)
+        s.step(30)
+        fc, _, _ = c.state()
+        fs = s.distributions()
+    assert np.abs(fc - fs).max() <= 1e-12
+
+
+def test_colour_closed_box_conserves_phases(torch_cuda):
+    from paper_1806_10589_gb300 import ColorLattice
+
+    m = random_mask(12, 11, 10, 0.2, 8)
+    m[0] = 1
+    m[-1] = 1
+    ref = _case(m, 70, -1.0, closed=True)
+    a0, b0 = math.fsum(ref.A.ravel().tolist()), math.fsum(ref.B.ravel().tolist())
+    with ColorLattice(m, 1.0, 0.01, 0.9, -1.0, "fp64", stream=torch_cuda.cuda.current_stream()) as c:
+        c.set_state(ref.f, ref.A, ref.B)
+        c.step(300)
+        _, A, B = c.state()
+    assert abs(math.fsum(A.ravel().tolist()) - a0) <= 1e-12 * a0
+    assert abs(math.fsum(B.ravel().tolist()) - b0) <= 1e-12 * b0
+
+
+def test_laplace_law_static_droplet(torch_cuda):
+    """A droplet of phase A in phase B in a closed box: the pressure jump times
+    the radius is the same for two radii (Laplace law, Delta p = 2 gamma / R)."""
+    from paper_1806_10589_gb300 import ColorLattice
+
+    n = 48
+    m = np.zeros((n, n, n), np.uint8)
+    m[0] = 1
+    m[-1] = 1
+    m[:, 0] = 1
+    m[:, -1] = 1
+    m[:, :, 0] = 1
+    m[:, :, -1] = 1
+    c0 = (n - 1) / 2.0
+    z, y, x = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    r = np.sqrt((x - c0) ** 2 + (y - c0) ** 2 + (z - c0) ** 2)
+    out = []
+    for R in (9.0, 13.0):
+        ref = CO.ColourOracle(m, 1.0, alpha=0.01, beta=0.95, phi_s=-1.0, inlet=None, outlet=None)
+        ref.init_phase(np.where(r < R, 1.0, -1.0))
+        with ColorLattice(m, 1.0, 0.01, 0.95, -1.0, "fp32", stream=torch_cuda.cuda.current_stream()) as c:
+            c.set_state(ref.f, ref.A, ref.B)
+            c.step(4000)
+            rho, ux, uy, uz, phi = c.fields()
+        inside = (r < R - 4) & (m == 0)
+        outside = (r > R + 4) & (r < R + 10) & (m == 0)
+        dp = (rho[inside].mean() - rho[outside].mean()) / 3.0
+        out.append((R, dp, float(np.abs(np.stack([ux, uy, uz])).max())))
+    (R1, p1, u1), (R2, p2, u2) = out
+    assert p1 > 0 and p2 > 0, out
+    assert abs(p1 * R1 - p2 * R2) <= 0.15 * p1 * R1, out
+    assert max(u1, u2) < 0.05, out
