@@ -63,10 +63,15 @@ def workload():
     return mask, info, a_in
 
 
+STEP_KERNEL_SOURCES = ("lbm_api.cu", "lbm_device.cuh", "lbm_internal.h", "lbm_kernels.cu")
+
+
 def kernel_sources_sha():
+    """Hash of the sources that define the single-lattice step kernel and its
+    launch (other modules of the library do not change it)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1806_10589_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    for f in STEP_KERNEL_SOURCES:
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(f.encode() + b"\0" + fh.read())
     return h.hexdigest()[:16]
@@ -304,6 +309,68 @@ def run_ensemble(stream, prec="fp16dev", steps=2000, warmup=64):
             "max_inlet_flux_rel_err": max(abs(f - q) / q for f, q in zip(fl, Qs))}
 
 
+def laplace_gamma(stream, alpha=0.01, beta=0.95, n=48, R=12.0, steps=3000):
+    """Interfacial tension of the colour model for (alpha, beta): Laplace law
+    gamma = Delta p R / 2 for a static droplet of phase A in a closed box."""
+    from paper_1806_10589_gb300 import ColorLattice
+
+    m = np.zeros((n, n, n), np.uint8)
+    m[0], m[-1], m[:, 0], m[:, -1], m[:, :, 0], m[:, :, -1] = 1, 1, 1, 1, 1, 1
+    c0 = (n - 1) / 2.0
+    z, y, x = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    r = np.sqrt((x - c0) ** 2 + (y - c0) ** 2 + (z - c0) ** 2)
+    with ColorLattice(m, 1.0, alpha, beta, -1.0, "fp32", stream=stream) as c:
+        c.set_phase(np.where(r < R, 1.0, -1.0))
+        c.step(steps)
+        rho, _, _, _, _ = c.fields()
+    dp = (rho[(r < R - 4) & (m == 0)].mean() - rho[(r > R + 4) & (r < R + 10) & (m == 0)].mean()) / 3.0
+    return dp * R / 2.0
+
+
+def run_two_fluid(stream, steps=500, warmup=20):
+    """Colour-model step on a 192x192x384 seeded sphere pack (radii U[5,10],
+    porosity 0.35), FP32, initially saturated with the wetting phase B, the
+    non-wetting phase A injected at the flux of Ca = mu_w Q / (gamma eps A) = 1e-5
+    (Section 3.2), gamma from the Laplace calibration of (alpha, beta)."""
+    import torch
+
+    from paper_1806_10589_gb300 import ColorLattice
+
+    alpha, beta, tau = 0.01, 0.95, 1.0
+    gamma = laplace_gamma(stream, alpha, beta)
+    mask, info = sphere_pack((192, 192, 384), 5.0, 10.0, 0.35, seed=31, reservoir=6)
+    nz, ny, nx = mask.shape
+    eps = info["porosity"]
+    mu = (tau - 0.5) / 3.0
+    Q = 1e-5 * gamma * eps * (nx * ny) / mu
+    with ColorLattice(mask, tau, alpha, beta, -1.0, "fp32", stream=stream) as c:
+        c.set_phase(-np.ones(mask.shape))
+        c.set_flux_bc(Q, 1.0)
+        c.step(warmup)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        c.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        q_in, _ = c.get_flux(4)
+    n = int((mask == 0).sum())
+    unit = 82 * 4  # FP32 values per node and step: f 19+19, A/B 14+14, phase 1, pre-pass A/B 14 + phi 1
+    peak, _ = measured_hbm_peak()
+    ach = unit * n / (ms * 1e-3 / steps) / 1e9
+    return {"workload": "two-fluid colour model, 192x192x384 sphere pack (radii 5-10, porosity %.3f, 6+6 "
+                        "reservoir layers), tau 1, alpha %g, beta %g, wetting solid, non-wetting injected "
+                        "at Ca 1e-5, FP32" % (eps, alpha, beta),
+            "gamma_laplace": gamma, "Q": Q, "n_pore": n, "steps": steps,
+            "MLUPS": round(n * steps / (ms * 1e-3) / 1e6, 1), "ms_per_step": round(ms / steps, 5),
+            "roofline": {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(ach / peak, 4), "bytes_per_unit": unit,
+                         "kernels": "k_color_pre + k_color_step"},
+            "inlet_flux_rel_err": abs(q_in - Q) / Q}
+
+
 # ------------------------------------------------------------- our path ---
 def run_ours(args, rank, world, local):
     import torch
@@ -378,6 +445,10 @@ def run_ours(args, rank, world, local):
     if rank == 0 and args.ensemble:
         ens = run_ensemble(stream)
 
+    two = None
+    if rank == 0 and args.two_fluid:
+        two = run_two_fluid(stream)
+
     steady = None
     if rank == 0 and args.steady:
         steady = time_to_steady(mask, a_in, stream)
@@ -416,6 +487,7 @@ def run_ours(args, rank, world, local):
         "gpu_launches": K + (2 * (K // 1024) if prec in ("fp16dev", "bf16dev") else 0),
         "time_to_steady": steady,
         "ensemble": ens,
+        "two_fluid": two,
         "clocks": clk,
         "check": {"q_in": q_in, "Q": Q, "rho_in": rho_in, "u_max": mon["u_max"], "status": mon["status"]},
     }
@@ -534,6 +606,8 @@ def main(argv=None):
                     help="also run the time-to-steady-flux comparison (FP32 / FP16 / BF16)")
     ap.add_argument("--ensemble", action=argparse.BooleanOptionalAction, default=True,
                     help="also time the batched 64-member ensemble (FP16 deviation storage)")
+    ap.add_argument("--two-fluid", action=argparse.BooleanOptionalAction, default=True,
+                    help="also time the two-fluid colour model on a 192x192x384 pack")
     ap.add_argument("--warmstart", action="store_true",
                     help="run the learned warm-start experiment instead of the benchmark")
     ap.add_argument("--ws-samples", type=int, default=512)

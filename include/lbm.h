@@ -238,6 +238,9 @@ int lbm_color_create(const uint8_t* mask, int nx, int ny, int nz, double tau, do
 int lbm_color_set_stream(lbm_color* c, void* cuda_stream);
 /* Inlet flux Q (Eq. flux, Eq. potential) and the phase phi_in of the injected fluid. */
 int lbm_color_set_flux_bc(lbm_color* c, double Q, double phi_in);
+/* Rest state with a phase field: host phi (nx*ny*nz doubles in [-1, 1]) and optional
+ * rho (NULL = 1): f = f^eq(rho, 0), A = w7 rho (1 + phi)/2, B = w7 rho (1 - phi)/2. */
+int lbm_color_set_phase(lbm_color* c, const double* phi, const double* rho);
 /* Whole state from/to host arrays [q][z][y][x]: f 19, A 7 and B 7 planes of nx*ny*nz doubles. */
 int lbm_color_set_state(lbm_color* c, const double* f, const double* A, const double* B);
 int lbm_color_get_state(lbm_color* c, double* f, double* A, double* B);

@@ -289,6 +289,22 @@ __global__ void k_color_face_flux(const T* __restrict__ f, DevLattice L, int whi
     }
 }
 
+// Rest state with a phase field: f = f^eq(rho, 0), A = w7 rho (1 + phi)/2,
+// B = w7 rho (1 - phi)/2 (pore order inputs).
+template <class T>
+__global__ void k_color_init(T* __restrict__ f, T* __restrict__ A, T* __restrict__ B, DevLattice L,
+                             const double* __restrict__ phi, const double* __restrict__ rho) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= L.n) return;
+    const double r = rho ? rho[i] : 1.0;
+    const double ph = phi[i];
+    for (int q = 0; q < 19; ++q) f[(int64_t)q * L.ns + i] = (T)(wq(q) * (r - 1.0));
+    for (int q = 0; q < 7; ++q) {
+        A[(int64_t)q * L.ns + i] = (T)(w7(q) * r * (1.0 + ph) * 0.5);
+        B[(int64_t)q * L.ns + i] = (T)(w7(q) * r * (1.0 - ph) * 0.5);
+    }
+}
+
 thread_local std::string g_color_err;
 
 }  // namespace
@@ -556,6 +572,35 @@ int lbm_color_set_state(lbm_color* c, const double* f, const double* A, const do
     COLOR_CUDA(c, up(c->f[c->cur], hf));
     COLOR_CUDA(c, up(c->A[c->cur], ha));
     COLOR_CUDA(c, up(c->B[c->cur], hb));
+    c->steps = 0;
+    return LBM_OK;
+}
+
+int lbm_color_set_phase(lbm_color* c, const double* phi, const double* rho) {
+    int rc = center(c);
+    if (rc) return rc;
+    if (!phi) return cfail(c, LBM_EINVAL, "NULL phi");
+    const int64_t n = c->L.n;
+    std::vector<double> h((size_t)(2 * n), 1.0);
+    for (int64_t i = 0; i < n; ++i) {
+        const double v = phi[(size_t)c->pore_voxel[(size_t)i]];
+        if (!(v >= -1.0) || !(v <= 1.0)) return cfail(c, LBM_EINVAL, "phi must lie in [-1, 1]");
+        h[(size_t)i] = v;
+        if (rho) h[(size_t)(n + i)] = rho[(size_t)c->pore_voxel[(size_t)i]];
+    }
+    double* d = nullptr;
+    COLOR_CUDA(c, cudaMalloc(&d, h.size() * sizeof(double)));
+    cudaError_t e = cudaMemcpyAsync(d, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cdispatch(c->prec, [&](auto zero) {
+            using T = decltype(zero);
+            lbm::k_color_init<T><<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(
+                (T*)c->f[c->cur], (T*)c->A[c->cur], (T*)c->B[c->cur], c->L, d, d + n);
+            return cudaGetLastError();
+        });
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(d);
+    if (e != cudaSuccess) return cfail(c, LBM_ECUDA, "lbm_color_set_phase: %s", cudaGetErrorString(e));
     c->steps = 0;
     return LBM_OK;
 }

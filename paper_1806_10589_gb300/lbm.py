@@ -70,6 +70,7 @@ SIGNATURES = {
                                    C.c_double, C.c_double, C.c_int, C.POINTER(_P)]),
     "lbm_color_set_stream": (C.c_int, [_P, _P]),
     "lbm_color_set_flux_bc": (C.c_int, [_P, C.c_double, C.c_double]),
+    "lbm_color_set_phase": (C.c_int, [_P, _DP, _DP]),
     "lbm_color_set_state": (C.c_int, [_P, _DP, _DP, _DP]),
     "lbm_color_get_state": (C.c_int, [_P, _DP, _DP, _DP]),
     "lbm_color_step": (C.c_int, [_P, C.c_int]),
@@ -472,6 +473,11 @@ class ColorLattice:
 
     def set_flux_bc(self, Q, phi_in=1.0):
         self._check(self._lib.lbm_color_set_flux_bc(self._h, float(Q), float(phi_in)))
+
+    def set_phase(self, phi, rho=None):
+        phi = np.ascontiguousarray(phi, dtype=np.float64).reshape(self.shape)
+        rho = None if rho is None else np.ascontiguousarray(rho, dtype=np.float64).reshape(self.shape)
+        self._check(self._lib.lbm_color_set_phase(self._h, _ptr(phi, C.c_double), _ptr(rho, C.c_double)))
 
     def set_state(self, f, A, B):
         cv = [np.ascontiguousarray(a, dtype=np.float64) for a in (f, A, B)]
