@@ -225,10 +225,13 @@ const char* lbm_last_error(const lbm_ctx* ctx);
  * Phases: D3Q7 A and B (w0 = 1/3, w1..6 = 1/9) with the recolouring update
  * A_q(x + xi_q) = w_q N_A [1 + 9/2 u.xi_q + beta N_B n.xi_q] (B with -beta N_A),
  * phi = (N_A - N_B)/(N_A + N_B).  Readings of the silent points: C is the
- * isotropic D3Q19 stencil 3 sum_q w_q xi_q phi(x + xi_q), a solid neighbour
- * contributes phi_s (wetting: +1 = the solid looks like phase A), a z-outside
- * neighbour the node's own phi; the inlet injects phase fraction phi_in, the
- * outlet lets both phases leave with their local composition.  FP64 or FP32
+ * isotropic D3Q19 stencil 3 sum_q w_q xi_q phi(x + xi_q), a solid voxel
+ * contributes phi_s (wetting: +1 = the solid looks like phase A), a neighbour
+ * outside the box (any face) the node's own phi, so the box faces are
+ * wetting-neutral walls (they still bounce momentum and phases back); the inlet plane holds the injected composition
+ * (N_A = rho_in (1 + phi_in)/2, N_B = rho_in (1 - phi_in)/2, set on the value that
+ * entered through the inlet), the outlet lets both phases leave with their local
+ * composition.  FP64 or FP32
  * storage.  A mask whose z = 0 (z = nz-1) plane is all solid has no inlet
  * (outlet) condition, so closed boxes are allowed.
  * ------------------------------------------------------------------------- */

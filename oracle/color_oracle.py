@@ -18,14 +18,18 @@ Per step, on the pore nodes of a voxel mask:
 
 Readings where the paper is silent (also listed in the design notes):
   * the gradient is the isotropic D3Q19 stencil C = 3 sum_q w_q xi_q phi(x + xi_q);
-    a solid (or lateral out-of-box) neighbour contributes phi_s (the wetting
-    parameter: phi_s = +1 means the solid looks like phase A), a z out-of-box
-    neighbour contributes the node's own phi; n = 0 where |C| = 0;
+    a solid voxel contributes phi_s (the wetting parameter: phi_s = +1 means the
+    solid looks like phase A), a neighbour outside the box (through any face)
+    contributes the node's own phi, so the box faces are wetting-neutral; n = 0
+    where |C| = 0;
   * D3Q7 values pushed into a solid (or lateral outside) bounce back to the
-    sender in the opposite direction; at the inlet the entering value is
-    w5 N [1 + 9/2 u_z] with N_A = rho_in (1 + phi_in)/2, N_B = rho_in (1 - phi_in)/2
-    (phi_in = +1: the non-wetting phase A is injected); at the outlet the
-    entering value is w6 N [1 - 9/2 u_z] with the node's own N_A, N_B, u_z;
+    sender in the opposite direction; the inlet plane holds the injected
+    composition: at the start of every step the D3Q7 value that entered an inlet
+    node through the inlet (direction 5) is set so that the node carries
+    N_A = rho_in (1 + phi_in)/2 and N_B = rho_in (1 - phi_in)/2, rho_in the inlet
+    density of the previous step (phi_in = +1: the non-wetting phase A is
+    injected); at the outlet the entering value is w6 N [1 - 9/2 u_z] with the
+    node's own N_A, N_B, u_z;
   * the collision uses the velocity and colour field of the same step; the
     mass transport uses u = j after the boundary closures.
 """
@@ -47,15 +51,12 @@ def colour_gradient(phi, mask, phi_s):
     nz, ny, nx = mask.shape
     solid = mask.astype(bool)
     field = np.where(solid, phi_s, phi)
-    padded = np.pad(field, 1, constant_values=phi_s)
+    padded = np.pad(field, 1, constant_values=np.nan)  # nan marks "outside the box"
     C = np.zeros((3,) + mask.shape)
     for q in range(1, L.NQ):
         cx, cy, cz = (int(v) for v in L.XI[q])
-        nb = padded[1 + cz:1 + cz + nz, 1 + cy:1 + cy + ny, 1 + cx:1 + cx + nx].copy()
-        if cz == 1:
-            nb[nz - 1] = phi[nz - 1]
-        elif cz == -1:
-            nb[0] = phi[0]
+        nb = padded[1 + cz:1 + cz + nz, 1 + cy:1 + cy + ny, 1 + cx:1 + cx + nx]
+        nb = np.where(np.isnan(nb), phi, nb)
         for a in range(3):
             if L.XI[q, a]:
                 C[a] += 3.0 * L.W[q] * L.XI[q, a] * nb
@@ -74,9 +75,9 @@ def colour_gradient_loops(phi, mask, phi_s):
                     continue
                 for q in range(1, L.NQ):
                     sx, sy, sz = x + L.XI[q, 0], y + L.XI[q, 1], z + L.XI[q, 2]
-                    if sz < 0 or sz >= nz:
+                    if sz < 0 or sz >= nz or sx < 0 or sx >= nx or sy < 0 or sy >= ny:
                         v = phi[z, y, x]
-                    elif sx < 0 or sx >= nx or sy < 0 or sy >= ny or mask[sz, sy, sx]:
+                    elif mask[sz, sy, sx]:
                         v = phi_s
                     else:
                         v = phi[sz, sy, sx]
@@ -146,7 +147,19 @@ class ColourOracle:
         for _ in range(n):
             self._step_once()
 
+    def hold_inlet_composition(self):
+        """Set the D3Q7 value that entered each inlet node through the inlet
+        (direction 5) so the node carries N_A = rho_in (1 + phi_in)/2 and
+        N_B = rho_in (1 - phi_in)/2 (reading above)."""
+        frac = (1.0 + self.phi_in) / 2.0
+        pore0 = self.pore[0]
+        for arr, target in ((self.A, self.rho_in * frac), (self.B, self.rho_in * (1.0 - frac))):
+            others = arr[:, 0].sum(axis=0) - arr[5, 0]
+            arr[5, 0] = np.where(pore0, target - others, 0.0)
+
     def _step_once(self):
+        if self.inlet is not None:
+            self.hold_inlet_composition()
         phi, NA, NB = self.phase_field()
         C = colour_gradient(phi, self.mask, self.phi_s)
         dm, nvec = interfacial_moments(C)
@@ -197,10 +210,9 @@ class ColourOracle:
             sl = (slice(1 - cz, 1 - cz + nz), slice(1 - cy, 1 - cy + ny), slice(1 - cx, 1 - cx + nx))
             src = np.pad(out[q], 1)[sl]
             new[q] = np.where(solid_pad[sl], out[OPP7[q]], src)
-            if cz == 1:  # entering through the inlet plane
+            if cz == 1:  # entering through the inlet plane: set at the next step's start
                 if self.inlet is not None:
-                    frac = (1.0 + self.phi_in) / 2.0 if is_a else (1.0 - self.phi_in) / 2.0
-                    new[q, 0] = W7[q] * self.rho_in * frac * (1.0 + 4.5 * u[2, 0])
+                    new[q, 0] = 0.0
             elif cz == -1:  # entering through the outlet plane
                 if self.outlet is not None:
                     N = NA[nz - 1] if is_a else NB[nz - 1]

@@ -6,12 +6,14 @@
 //                 pulled momentum distributions (FP64 sum, last-block finish);
 //   k_color_step  pull of the 19 momentum distributions with halfway bounce-back,
 //                 Appendix B closures, colour gradient C = 3 sum_q w_q xi_q phi(x+xi_q)
-//                 (solid neighbours give phi_s, z-outside neighbours the node's own
-//                 phi), MRT collision with the interfacial equilibrium terms, then
+//                 (solid voxels give phi_s, neighbours outside the box the node's
+//                 own phi: the box faces are wetting-neutral), MRT collision with the interfacial equilibrium terms, then
 //                 the D3Q7 mass transport: every node pushes
 //                 A_q = w_q N_A [1 + 9/2 u.xi_q + beta N_B n.xi_q] (and B with -beta N_A)
-//                 to x + xi_q, bouncing back from solids; the inlet injects
-//                 w5 rho_in N_frac (1 + 9/2 u_z), the outlet takes w6 N (1 - 9/2 u_z).
+//                 to x + xi_q, bouncing back from solids and lateral box faces; the outlet takes
+//                 w6 N (1 - 9/2 u_z).  The inlet plane holds the injected
+//                 composition: the pre-pass sets the value that entered each inlet
+//                 node through the inlet so the node carries rho_in (1 +- phi_in)/2.
 // Momentum distributions are stored shifted (d = f - w) as in the single-fluid
 // path; A and B are stored as they are.
 #include <cuda_runtime.h>
@@ -33,6 +35,9 @@ namespace lbm {
 namespace {
 
 constexpr int kCB = 256;
+// Lateral out-of-box cell of the colour grid: a wall for momentum and mass
+// transport (bounce-back) but wetting-neutral in the colour gradient.
+constexpr int kSideOut = -3;
 
 struct ColorParams {
     double Q;         // prescribed inlet flux
@@ -98,7 +103,7 @@ __host__ __device__ constexpr double mnorm2(int k) {
 
 template <class T>
 __global__ void __launch_bounds__(kCB)
-k_color_pre(const T* __restrict__ f, const T* __restrict__ A, const T* __restrict__ B, T* __restrict__ phi,
+k_color_pre(const T* __restrict__ f, T* __restrict__ A, T* __restrict__ B, T* __restrict__ phi,
             DevLattice L, ColorParams* prm, double* __restrict__ partials, unsigned* __restrict__ counter) {
     __shared__ double sh[32];
     __shared__ bool last;
@@ -109,8 +114,19 @@ k_color_pre(const T* __restrict__ f, const T* __restrict__ A, const T* __restric
         T na = 0, nb = 0;
 #pragma unroll
         for (int q = 0; q < 7; ++q) {
+            if (q == 5 && i64 < L.a_in) continue;
             na += A[(int64_t)q * L.ns + i];
             nb += B[(int64_t)q * L.ns + i];
+        }
+        if (i64 < L.a_in) {
+            // injected composition: the density of the previous step (read before
+            // this launch's last block replaces it)
+            const T rin = T(1) + T(prm->drho_in);
+            const T fa = (T(1) + T(prm->phi_in)) * T(0.5);
+            A[(int64_t)5 * L.ns + i] = rin * fa - na;
+            B[(int64_t)5 * L.ns + i] = rin * (T(1) - fa) - nb;
+            na = rin * fa;
+            nb = rin * (T(1) - fa);
         }
         phi[i] = (na - nb) / (na + nb);
         if (i64 < L.a_in) {
@@ -166,7 +182,7 @@ k_color_step(const T* __restrict__ fin, T* __restrict__ fout, const T* __restric
         const int id = __ldg(L.grid + p + grid_off<Q>(L.sy, L.sz));
         d[Q] = id >= 0 ? fin[(int64_t)Q * L.ns + id] : fin[(int64_t)opp(Q) * L.ns + i];
         // colour-gradient neighbour x + xi_opp(Q) is the pull source of Q
-        const T ph = id >= 0 ? phi[id] : (id == SOLID ? phi_s : phi_own);
+        const T ph = id >= 0 ? phi[id] : (id == SOLID ? phi_s : phi_own);  // box faces: own phi
         constexpr int R = opp(Q);  // this neighbour sits at x + xi_R
         const T wq3 = T(3.0 * wq(R));
         if (cx(R)) cgx += wq3 * T(cx(R)) * ph;
@@ -218,17 +234,15 @@ k_color_step(const T* __restrict__ fin, T* __restrict__ fout, const T* __restric
             if (id >= 0) {
                 Aout[(int64_t)Q * L.ns + id] = va;
                 Bout[(int64_t)Q * L.ns + id] = vb;
-            } else if (id == SOLID) {
+            } else if (id != ZOUT) {  // solid voxel or lateral box face: bounce back
                 Aout[(int64_t)opp(Q) * L.ns + i] = va;
                 Bout[(int64_t)opp(Q) * L.ns + i] = vb;
             }
         }
     });
-    if (inlet) {  // the value entering through the inlet plane (direction 5)
-        const T rin = T(1) + T(prm->drho_in);
-        const T fa = (T(1) + T(prm->phi_in)) * T(0.5);
-        Aout[(int64_t)5 * L.ns + i] = T(w7(5)) * rin * fa * (T(1) + T(4.5) * jz);
-        Bout[(int64_t)5 * L.ns + i] = T(w7(5)) * rin * (T(1) - fa) * (T(1) + T(4.5) * jz);
+    if (inlet) {  // the value entering through the inlet plane: set by the next pre-pass
+        Aout[(int64_t)5 * L.ns + i] = T(0);
+        Bout[(int64_t)5 * L.ns + i] = T(0);
     }
     if (outlet) {  // the value entering through the outlet plane (direction 6)
         Aout[(int64_t)6 * L.ns + i] = T(w7(6)) * na * (T(1) - T(4.5) * jz);
@@ -401,7 +415,7 @@ int cstep_once(lbm_color* c) {
     const int k = c->cur;
     cudaError_t e = cdispatch(c->prec, [&](auto zero) {
         using T = decltype(zero);
-        lbm::k_color_pre<T><<<nb, lbm::kCB, 0, c->stream>>>((const T*)c->f[k], (const T*)c->A[k], (const T*)c->B[k],
+        lbm::k_color_pre<T><<<nb, lbm::kCB, 0, c->stream>>>((const T*)c->f[k], (T*)c->A[k], (T*)c->B[k],
                                                            (T*)c->phi, c->L, c->d_prm, c->d_partials, c->d_counter);
         lbm::k_color_step<T><<<nb, lbm::kCB, 0, c->stream>>>(
             (const T*)c->f[k], (T*)c->f[k ^ 1], (const T*)c->A[k], (T*)c->A[k ^ 1], (const T*)c->B[k],
@@ -445,11 +459,13 @@ int lbm_color_create(const uint8_t* mask, int nx, int ny, int nz, double tau, do
     c->beta = beta;
     c->phi_s = phi_s;
     std::vector<int> grid((size_t)(px * py * pz), lbm::SOLID);
-    for (int64_t y = 0; y < py; ++y)
-        for (int64_t x = 0; x < px; ++x) {
-            grid[(size_t)(y * px + x)] = lbm::ZOUT;
-            grid[(size_t)(((pz - 1) * py + y) * px + x)] = lbm::ZOUT;
-        }
+    for (int64_t z = 0; z < pz; ++z)
+        for (int64_t y = 0; y < py; ++y)
+            for (int64_t x = 0; x < px; ++x)
+                if (z == 0 || z == pz - 1)
+                    grid[(size_t)((z * py + y) * px + x)] = lbm::ZOUT;
+                else if (x == 0 || x == px - 1 || y == 0 || y == py - 1)
+                    grid[(size_t)((z * py + y) * px + x)] = lbm::kSideOut;
     std::vector<uint32_t> vox;
     int64_t a_in = 0, a_out = 0;
     for (int64_t z = 0; z < nz; ++z)
@@ -667,8 +683,8 @@ int lbm_color_get_fields(lbm_color* c, double* rho, double* ux, double* uy, doub
             lbm::ColorParams* none = c->d_prm;
             lbm::DevLattice L0 = c->L;
             L0.a_in = 0;  // no inlet reduction in this refresh
-            lbm::k_color_pre<T><<<nb, lbm::kCB, 0, c->stream>>>((const T*)c->f[c->cur], (const T*)c->A[c->cur],
-                                                               (const T*)c->B[c->cur], (T*)c->phi, L0, none,
+            lbm::k_color_pre<T><<<nb, lbm::kCB, 0, c->stream>>>((const T*)c->f[c->cur], (T*)c->A[c->cur],
+                                                               (T*)c->B[c->cur], (T*)c->phi, L0, none,
                                                                c->d_partials, c->d_counter);
             lbm::k_color_export<T><<<nb, lbm::kCB, 0, c->stream>>>((const T*)c->f[c->cur], (const T*)c->phi, c->L,
                                                                   c->d_voxel, d, d + ncell, d + 2 * ncell,

@@ -82,3 +82,36 @@ def test_inlet_flux_exact_two_phase():
         _, _, _, uz, _ = c.fields()
         A = int((m[0] == 0).sum())
         assert abs(math.fsum(uz[0][m[0] == 0].tolist()) - 0.01) <= 8 * A * np.finfo(float).eps
+
+
+def test_box_faces_are_wetting_neutral_and_solids_wet():
+    """A uniform phase field has no colour gradient at the box faces whatever
+    phi_s is; next to a solid voxel the gradient points away from the solid
+    when phi_s < phi (the solid looks like phase B)."""
+    m = np.zeros((5, 6, 7), np.uint8)
+    phi = np.full(m.shape, 0.3)
+    for ps in (-1.0, 0.0, 1.0):
+        np.testing.assert_allclose(CO.colour_gradient(phi, m, ps), 0.0, atol=1e-15)
+    m[2, 3, 3] = 1
+    C = CO.colour_gradient(phi, m, -1.0)
+    # the +x neighbour of the solid: C_x > 0 and C_y = C_z = 0 by symmetry
+    assert C[0, 2, 3, 4] > 0
+    assert abs(C[1, 2, 3, 4]) < 1e-15 and abs(C[2, 2, 3, 4]) < 1e-15
+    # stencil weight of one face neighbour: 3 w_1 (phi - phi_s) = (1/6) * 1.3
+    np.testing.assert_allclose(C[0, 2, 3, 4], 3.0 / 18.0 * 1.3, rtol=1e-14)
+
+
+def test_inlet_plane_holds_injected_composition():
+    m = duct_mask(6, 6, 8)
+    c = CO.ColourOracle(m, 0.9, alpha=0.005, beta=0.95, phi_s=-1.0, Q=0.01, phi_in=0.6)
+    c.init_phase(np.tanh(uniform_field(m.shape, 3)))
+    c.step(3)
+    before_A, before_B = c.A.copy(), c.B.copy()
+    c.hold_inlet_composition()
+    _, NA, NB = c.phase_field()
+    p0 = m[0] == 0
+    np.testing.assert_allclose(NA[0][p0], c.rho_in * 0.8, rtol=1e-14)
+    np.testing.assert_allclose(NB[0][p0], c.rho_in * 0.2, rtol=1e-14)
+    # only the value entering through the inlet plane changed
+    changed = (c.A != before_A) | (c.B != before_B)
+    assert not changed[:5].any() and not changed[6].any() and not changed[5, 1:].any()

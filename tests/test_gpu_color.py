@@ -1,6 +1,7 @@
 """GPU parity of the two-fluid colour model (lbm_color_*) against the FP64 colour
 oracle, its single-phase limit against the single-fluid path, phase mass
-conservation in a closed box, and the Laplace law of a static droplet.
+conservation in a closed box, the Laplace law of a static droplet and the
+drainage rate of Section 3.2.
 
 Tolerances: FP64 1e-11 relative (as the single-fluid path); FP32 the same
 per-step budget as the single-fluid FP32 test (20 N eps32 of the largest
@@ -148,30 +149,48 @@ def test_laplace_law_static_droplet(torch_cuda):
     print("LAPLACE", out)
 
 
-def test_drainage_rate_matches_flux(torch_cuda):
-    """Section 3.2 (square-tube drainage): a tube whose first 6 layers hold the
-    non-wetting phase A and the rest the wetting phase B, walls wetting, A
-    injected at the flux Q.  Once the displacement is established the wetting
-    volume leaves at the prescribed rate, -d V_w / dt = Q (eps V ds_w/dt = Q),
-    while the inlet flux itself is exact every step."""
+def _capillary_tube(n, length, reservoir=6):
+    """Section 3.2 geometry: a square tube (solid-voxel walls) between a
+    non-wetting and a wetting reservoir of `reservoir` pure-fluid layers each."""
+    m = np.zeros((length + 2 * reservoir, n, n), np.uint8)
+    t = slice(reservoir, reservoir + length)
+    m[t, 0, :] = 1
+    m[t, -1, :] = 1
+    m[t, :, 0] = 1
+    m[t, :, -1] = 1
+    return m
+
+
+@pytest.mark.parametrize("Q", [0.02, 0.2])
+def test_drainage_rate_matches_flux(torch_cuda, Q):
+    """Section 3.2 (primary drainage of a square tube): the non-wetting phase A
+    fills the inlet reservoir, the wetting phase B the tube and the outlet
+    reservoir, the tube walls are wetting (phi_s = -1) and A is injected at the
+    flux Q with the paper's lattice surface tension (gamma ~ 6e-5, i.e. alpha =
+    5.9e-5 by the Laplace calibration gamma ~ 1.02 alpha).  Once the displacement
+    is steady the wetting mass leaves at the prescribed rate,
+    -d(eps V s_w)/dt = Q, while the inlet flux is exact every step."""
     from paper_1806_10589_gb300 import ColorLattice
 
-    m = duct_mask(20, 20, 60)
-    Q = 0.02
-    z = np.arange(60)[:, None, None] * np.ones(m.shape)
-    with ColorLattice(m, 1.0, 0.01, 0.95, -1.0, "fp32", stream=torch_cuda.cuda.current_stream()) as c:
+    m = _capillary_tube(20, 48)
+    pore = m == 0
+    z = np.arange(m.shape[0])[:, None, None] * np.ones(m.shape)
+    with ColorLattice(m, 1.0, 5.9e-5, 0.95, -1.0, "fp32", stream=torch_cuda.cuda.current_stream()) as c:
         c.set_phase(np.where(z < 6, 1.0, -1.0))
         c.set_flux_bc(Q, 1.0)
 
-        def wetting_volume():
-            rho, _, _, _, phi = c.fields()
-            return float((rho * (1.0 - phi) / 2.0)[m == 0].sum())
+        def wetting_mass():
+            _, _, B = c.state()
+            NB = B.sum(axis=0)
+            return float(NB[pore].sum()), float(NB[0][pore[0]].sum())
 
+        c.step(2000)
+        v1, _ = wetting_mass()
         c.step(4000)
-        v1 = wetting_volume()
+        v2, b_inlet = wetting_mass()
         q_in, _ = c.get_flux(4)
-        c.step(10000)
-        v2 = wetting_volume()
-    rate = (v1 - v2) / 10000.0
+    rate = (v1 - v2) / 4000.0
     assert abs(q_in - Q) <= 1e-4 * Q
-    assert abs(rate - Q) <= 0.1 * Q, (rate, Q)
+    assert abs(rate - Q) <= 0.02 * Q, (rate, Q)
+    # no wetting phase reaches the inlet plane (it would be replaced by A there)
+    assert b_inlet <= 1e-2 * Q, b_inlet
