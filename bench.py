@@ -334,15 +334,14 @@ def run_two_fluid(stream, steps=500, warmup=20):
     (Section 3.2), gamma from the Laplace calibration of (alpha, beta)."""
     import torch
 
-    from paper_1806_10589_gb300 import ColorLattice
+    from paper_1806_10589_gb300 import ColorLattice, drainage
 
     alpha, beta, tau = 0.01, 0.95, 1.0
     gamma = laplace_gamma(stream, alpha, beta)
     mask, info = sphere_pack((192, 192, 384), 5.0, 10.0, 0.35, seed=31, reservoir=6)
     nz, ny, nx = mask.shape
     eps = info["porosity"]
-    mu = (tau - 0.5) / 3.0
-    Q = 1e-5 * gamma * eps * (nx * ny) / mu
+    Q = drainage.simulated_flux(1e-5, eps, nx * ny, gamma, drainage.lattice_viscosity(tau))
     with ColorLattice(mask, tau, alpha, beta, -1.0, "fp32", stream=stream) as c:
         c.set_phase(-np.ones(mask.shape))
         c.set_flux_bc(Q, 1.0)
