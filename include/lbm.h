@@ -87,11 +87,18 @@ int lbm_set_pressure_bc(lbm_ctx* ctx, int face, double rho);
  * handle) for all later device work of this context.  NULL = default stream. */
 int lbm_set_stream(lbm_ctx* ctx, void* cuda_stream);
 
-/* Select the step-kernel variant (a tuning knob; every variant computes the
- * same step): 0 = one thread per pore node; 1 = persistent kernel whose
- * neighbour ids and pulled values are staged in shared memory by cp.async one
- * 256-node tile ahead (the default); 2 = the same with 128-node tiles.
- * Unknown variants return LBM_EINVAL.  Synchronises. */
+/* Select the step-kernel variant (every variant computes the same step, bit
+ * for bit): 0 = one thread per pore node (the default); 1 = persistent kernel
+ * whose neighbour ids and pulled values are staged in shared memory by cp.async
+ * one 256-node tile ahead; 2 = the same with 128-node tiles; 3 = AA pattern:
+ * ONE distribution buffer updated in place (the second buffer is freed, so the
+ * state needs half the memory), alternating a gather-scatter step and a
+ * node-local step; FP64/FP32 storage only (LBM_EUNSUPPORTED otherwise).  Each
+ * lbm_step call on variant 3 adds two in-place layout swaps (three for an odd
+ * step count), so that between calls the state reads exactly as with the
+ * other variants.  Leaving variant 3 allocates the second buffer again
+ * (LBM_ENOMEM if that fails; the context stays on variant 3).  Unknown
+ * variants return LBM_EINVAL.  Synchronises. */
 int lbm_set_kernel(lbm_ctx* ctx, int variant);
 
 /* Advance n >= 0 time steps, asynchronously on the context's stream.  One step

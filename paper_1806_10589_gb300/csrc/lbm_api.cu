@@ -43,7 +43,8 @@ struct lbm_ctx {
     lbm::StepConfig step_cfg{0, 0};
     lbm::DevLattice L{};
     void* f[2] = {nullptr, nullptr};
-    int cur = 0;
+    int cur = 0;     // buffer of the state (pull variants) and parity of the inlet-density slot
+    bool aa = false; // AA pattern: the state lives in f[0] alone, f[1] is released
     uint32_t* d_vox = nullptr;
     int* d_grid = nullptr;
     lbm::BcState h_bc{};
@@ -98,6 +99,9 @@ int enter(lbm_ctx* c) {
     return LBM_OK;
 }
 
+// Buffer that holds the current state (pull layout in every variant).
+void* state_f(lbm_ctx* c) { return c->aa ? c->f[0] : c->f[c->cur]; }
+
 int push_bc(lbm_ctx* c) {
     LBM_CUDA(c, cudaMemcpyAsync(c->d_bc, &c->h_bc, sizeof(lbm::BcState), cudaMemcpyHostToDevice,
                                 c->stream));
@@ -107,8 +111,17 @@ int push_bc(lbm_ctx* c) {
 }
 
 int one_step(lbm_ctx* c, cudaStream_t st) {
-    LBM_CUDA(c, lbm::launch_step_cfg(c->prec, c->step_cfg, c->f[c->cur], c->f[c->cur ^ 1], c->cur, c->L,
+    LBM_CUDA(c, lbm::launch_step_cfg(c->prec, c->step_cfg, state_f(c), c->f[c->cur ^ 1], c->cur, c->L,
                                      c->relax, c->d_bc, c->d_red_partials, c->d_step_counter, st));
+    c->cur ^= 1;
+    return LBM_OK;
+}
+
+// AA pattern: step number k of a call (k = 0 first) is odd-type (gather-scatter)
+// for even k and node-local for odd k; the call's layout swaps surround them.
+int aa_step(lbm_ctx* c, int64_t k, cudaStream_t st) {
+    LBM_CUDA(c, lbm::launch_aa_step(c->prec, c->f[0], (k & 1) == 0, c->cur, c->L, c->relax, c->d_bc,
+                                    c->d_red_partials, c->d_step_counter, st));
     c->cur ^= 1;
     return LBM_OK;
 }
@@ -116,7 +129,7 @@ int one_step(lbm_ctx* c, cudaStream_t st) {
 // Inlet density for the current buffer when the state or Q changed outside a
 // step (steps produce the next density themselves).
 int prime_inlet(lbm_ctx* c) {
-    LBM_CUDA(c, lbm::launch_inlet_reduce(c->prec, c->f[c->cur], c->cur, c->L, c->d_bc, c->d_red_partials,
+    LBM_CUDA(c, lbm::launch_inlet_reduce(c->prec, state_f(c), c->cur, c->L, c->d_bc, c->d_red_partials,
                                          c->d_red_counter, c->stream));
     return LBM_OK;
 }
@@ -126,7 +139,7 @@ int prime_inlet(lbm_ctx* c) {
 // the re-encoded values.  Asynchronous; a no-op for FP32/FP64.
 int maybe_reencode(lbm_ctx* c) {
     if (c->prec < LBM_PREC_FP16DEV || c->since_reencode < kReencodeInterval) return LBM_OK;
-    LBM_CUDA(c, lbm::launch_reencode(c->prec, c->f[c->cur], c->L, c->d_bc, c->ref_e, c->cur, c->stream));
+    LBM_CUDA(c, lbm::launch_reencode(c->prec, state_f(c), c->L, c->d_bc, c->ref_e, c->cur, c->stream));
     c->ref_e ^= 1;
     c->since_reencode = 0;
     return prime_inlet(c);
@@ -138,7 +151,7 @@ int build_graph(lbm_ctx* c, int parity) {
     cudaGraph_t g = nullptr;
     LBM_CUDA(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
     int rc = LBM_OK;
-    for (int k = 0; k < kGraphSteps && rc == LBM_OK; ++k) rc = one_step(c, c->cap_stream);
+    for (int k = 0; k < kGraphSteps && rc == LBM_OK; ++k) rc = c->aa ? aa_step(c, k, c->cap_stream) : one_step(c, c->cap_stream);
     cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
     c->cur = saved;
     if (rc != LBM_OK) {
@@ -153,7 +166,7 @@ int build_graph(lbm_ctx* c, int parity) {
 }
 
 int run_monitors(lbm_ctx* c, lbm::MonitorOut* out) {
-    LBM_CUDA(c, lbm::launch_monitors(c->prec, c->f[c->cur], c->L, c->d_bc, c->d_mon_partials, c->d_mon_counter,
+    LBM_CUDA(c, lbm::launch_monitors(c->prec, state_f(c), c->L, c->d_bc, c->d_mon_partials, c->d_mon_counter,
                                      c->d_mon, c->stream));
     LBM_CUDA(c, cudaMemcpyAsync(out, c->d_mon, sizeof(*out), cudaMemcpyDeviceToHost, c->stream));
     LBM_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -373,15 +386,29 @@ int lbm_set_stream(lbm_ctx* c, void* s) {
 int lbm_set_kernel(lbm_ctx* c, int variant) {
     int rc = enter(c);
     if (rc) return rc;
-    if (variant < 0 || variant > 2) return fail(c, LBM_EINVAL, "unknown step kernel variant %d", variant);
+    if (variant < 0 || variant > 3) return fail(c, LBM_EINVAL, "unknown step kernel variant %d", variant);
+    if (variant == 3 && c->prec != LBM_PREC_FP64 && c->prec != LBM_PREC_FP32)
+        return fail(c, LBM_EUNSUPPORTED, "the AA pattern stores FP64 or FP32 values");
     lbm::StepConfig cfg{};
-    LBM_CUDA(c, lbm::configure_step(c->prec, variant, c->L, &cfg));
+    if (variant < 3) LBM_CUDA(c, lbm::configure_step(c->prec, variant, c->L, &cfg));
     LBM_CUDA(c, cudaStreamSynchronize(c->stream));
     for (auto& g : c->graph)
         if (g) {
             cudaGraphExecDestroy(g);
             g = nullptr;
         }
+    if (variant == 3 && !c->aa) {
+        // keep the state buffer as f[0] (cur stays the inlet-density slot) and release the other
+        if (c->cur == 1) std::swap(c->f[0], c->f[1]);
+        LBM_CUDA(c, cudaFree(c->f[1]));
+        c->f[1] = nullptr;
+        c->aa = true;
+    } else if (variant < 3 && c->aa) {
+        const size_t fbytes = (size_t)19 * (size_t)c->L.ns * (size_t)lbm::elem_size(c->prec);
+        if ((rc = dev_alloc(c, &c->f[1], fbytes))) return rc;
+        if (c->cur == 1) std::swap(c->f[0], c->f[1]);  // the state must sit in f[cur]
+        c->aa = false;
+    }
     c->step_cfg = cfg;
     return LBM_OK;
 }
@@ -390,6 +417,22 @@ int lbm_step(lbm_ctx* c, int n) {
     int rc = enter(c);
     if (rc) return rc;
     if (n < 0) return fail(c, LBM_EINVAL, "n must be >= 0");
+    if (c->aa) {
+        if (n == 0) return LBM_OK;
+        LBM_CUDA(c, lbm::launch_aa_swap(c->prec, c->f[0], c->L, c->stream));
+        int k = 0;
+        while (n - k >= kGraphSteps) {
+            if (!c->graph[c->cur] && (rc = build_graph(c, c->cur))) return rc;
+            LBM_CUDA(c, cudaGraphLaunch(c->graph[c->cur], c->stream));
+            k += kGraphSteps;
+        }
+        for (; k < n; ++k)
+            if ((rc = aa_step(c, k, c->stream))) return rc;
+        if (n & 1) LBM_CUDA(c, lbm::launch_aa_unstream(c->prec, c->f[0], c->L, c->stream));
+        LBM_CUDA(c, lbm::launch_aa_swap(c->prec, c->f[0], c->L, c->stream));
+        c->steps += n;
+        return LBM_OK;
+    }
     int k = 0;
     while (n - k >= kGraphSteps) {
         if ((rc = maybe_reencode(c))) return rc;
@@ -413,12 +456,22 @@ int lbm_time_kernels(lbm_ctx* c, int n, float* ms_step, float* ms_inlet) {
     if (n < 1) return fail(c, LBM_EINVAL, "n must be >= 1");
     std::vector<cudaEvent_t> ev((size_t)2 * n, nullptr);
     for (auto& e : ev) LBM_CUDA(c, cudaEventCreate(&e));
+    if (c->aa) LBM_CUDA(c, lbm::launch_aa_swap(c->prec, c->f[0], c->L, c->stream));
     for (int k = 0; k < n; ++k) {
         LBM_CUDA(c, cudaEventRecord(ev[2 * k], c->stream));
-        LBM_CUDA(c, lbm::launch_step_cfg(c->prec, c->step_cfg, c->f[c->cur], c->f[c->cur ^ 1], c->cur, c->L,
-                                         c->relax, c->d_bc, c->d_red_partials, c->d_step_counter, c->stream));
+        if (c->aa) {
+            LBM_CUDA(c, lbm::launch_aa_step(c->prec, c->f[0], (k & 1) == 0, c->cur, c->L, c->relax, c->d_bc,
+                                            c->d_red_partials, c->d_step_counter, c->stream));
+        } else {
+            LBM_CUDA(c, lbm::launch_step_cfg(c->prec, c->step_cfg, state_f(c), c->f[c->cur ^ 1], c->cur, c->L,
+                                             c->relax, c->d_bc, c->d_red_partials, c->d_step_counter, c->stream));
+        }
         LBM_CUDA(c, cudaEventRecord(ev[2 * k + 1], c->stream));
         c->cur ^= 1;
+    }
+    if (c->aa) {
+        if (n & 1) LBM_CUDA(c, lbm::launch_aa_unstream(c->prec, c->f[0], c->L, c->stream));
+        LBM_CUDA(c, lbm::launch_aa_swap(c->prec, c->f[0], c->L, c->stream));
     }
     LBM_CUDA(c, cudaStreamSynchronize(c->stream));
     double t_st = 0.0;
@@ -458,7 +511,7 @@ int lbm_steady_residual(lbm_ctx* c, double* residual) {
         if ((rc = dev_alloc(c, &c->d_u_ref, (size_t)3 * c->L.n * sizeof(double)))) return rc;
         LBM_CUDA(c, cudaMemsetAsync(c->d_u_ref, 0, (size_t)3 * c->L.n * sizeof(double), c->stream));
     }
-    LBM_CUDA(c, lbm::launch_velocity_change(c->prec, c->f[c->cur], c->L, c->d_bc, c->d_u_ref, c->d_mon_partials,
+    LBM_CUDA(c, lbm::launch_velocity_change(c->prec, state_f(c), c->L, c->d_bc, c->d_u_ref, c->d_mon_partials,
                                             c->d_mon_counter, c->d_mon, c->stream));
     lbm::MonitorOut m{};
     LBM_CUDA(c, cudaMemcpyAsync(&m, c->d_mon, sizeof m, cudaMemcpyDeviceToHost, c->stream));
@@ -495,7 +548,7 @@ int lbm_get_fields(lbm_ctx* c, double* rho, double* ux, double* uy, double* uz) 
     double* outs[4] = {rho, ux, uy, uz};
     cudaError_t e = cudaMemsetAsync(d, 0, 4 * ncell * sizeof(double), c->stream);
     if (e == cudaSuccess)
-        e = lbm::launch_export(c->prec, c->f[c->cur], c->L, c->d_bc, d, d + ncell, d + 2 * ncell, d + 3 * ncell, 1,
+        e = lbm::launch_export(c->prec, state_f(c), c->L, c->d_bc, d, d + ncell, d + 2 * ncell, d + 3 * ncell, 1,
                                c->stream);
     for (int k = 0; k < 4 && e == cudaSuccess; ++k)
         if (outs[k])
@@ -514,7 +567,7 @@ int lbm_get_fields_device(lbm_ctx* c, float* rho, float* u) {
     const size_t ncell = (size_t)c->nx * c->ny * c->nz;
     if (rho) LBM_CUDA(c, cudaMemsetAsync(rho, 0, ncell * sizeof(float), c->stream));
     if (u) LBM_CUDA(c, cudaMemsetAsync(u, 0, 3 * ncell * sizeof(float), c->stream));
-    LBM_CUDA(c, lbm::launch_export(c->prec, c->f[c->cur], c->L, c->d_bc, rho, u, u ? u + ncell : nullptr,
+    LBM_CUDA(c, lbm::launch_export(c->prec, state_f(c), c->L, c->d_bc, rho, u, u ? u + ncell : nullptr,
                                    u ? u + 2 * ncell : nullptr, 0, c->stream));
     return LBM_OK;
 }
@@ -532,7 +585,7 @@ int lbm_set_fields(lbm_ctx* c, const double* rho, const double* ux, const double
     if ((rc = dev_alloc(c, &d, h.size() * sizeof(double)))) return rc;
     cudaError_t e = cudaMemcpyAsync(d, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess)
-        e = lbm::launch_init_eq(c->prec, c->f[c->cur], c->L, c->d_bc, rho ? d : nullptr, ux ? d + n : nullptr,
+        e = lbm::launch_init_eq(c->prec, state_f(c), c->L, c->d_bc, rho ? d : nullptr, ux ? d + n : nullptr,
                                 uy ? d + 2 * n : nullptr, uz ? d + 3 * n : nullptr, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     cudaFree(d);
@@ -550,7 +603,7 @@ int lbm_get_distributions(lbm_ctx* c, double* f) {
     std::vector<double> h((size_t)(19 * n));
     double* d = nullptr;
     if ((rc = dev_alloc(c, &d, h.size() * sizeof(double)))) return rc;
-    cudaError_t e = lbm::launch_decode(c->prec, c->f[c->cur], c->L, c->d_bc, d, c->stream);
+    cudaError_t e = lbm::launch_decode(c->prec, state_f(c), c->L, c->d_bc, d, c->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(h.data(), d, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -580,7 +633,7 @@ int lbm_set_distributions(lbm_ctx* c, const double* f) {
     double* d = nullptr;
     if ((rc = dev_alloc(c, &d, h.size() * sizeof(double)))) return rc;
     cudaError_t e = cudaMemcpyAsync(d, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream);
-    if (e == cudaSuccess) e = lbm::launch_encode(c->prec, c->f[c->cur], c->L, c->d_bc, d, c->stream);
+    if (e == cudaSuccess) e = lbm::launch_encode(c->prec, state_f(c), c->L, c->d_bc, d, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     cudaFree(d);
     if (e != cudaSuccess) return fail(c, LBM_ECUDA, "lbm_set_distributions: %s", cudaGetErrorString(e));
@@ -605,7 +658,7 @@ int lbm_inlet_density_noalloc(lbm_ctx* c, double* rho_in_device) {
         return fail(c, LBM_EINVAL,
                     "inlet has %lld pore nodes; lbm_inlet_density_noalloc supports at most %lld",
                     (long long)c->L.a_in, (long long)lbm::noalloc_max_inlet_nodes());
-    LBM_CUDA(c, lbm::launch_inlet_density_noalloc(c->prec, c->f[c->cur], c->L, c->d_bc, rho_in_device,
+    LBM_CUDA(c, lbm::launch_inlet_density_noalloc(c->prec, state_f(c), c->L, c->d_bc, rho_in_device,
                                                   c->stream));
     return LBM_OK;
 }

@@ -10,6 +10,8 @@
 //                   a deterministic last-block finish writes drho_in[slot ^ 1].
 //   k_inlet_reduce  the same density by a pull over the inlet plane, for states
 //                   set from outside a step (creation, set_*, a new Q).
+//   k_step_aa       the same step on ONE buffer (AA pattern, FP64/FP32), with
+//                   the layout swaps k_aa_swap / k_aa_unstream around a call.
 //   k_monitors      FP64 mass / flux / max|u| / NaN reductions of a state.
 //   k_export, k_init_eq, k_encode, k_decode   field and state conversions.
 #include <algorithm>
@@ -390,6 +392,161 @@ k_step(const StepPtrs<typename S::T> P, int slot, DevLattice L, typename S::M sp
                 bc->drho_in[slot ^ 1] = (bc->Q + s) / (double)L.a_in;
                 *counter = 0u;
             }
+        }
+    }
+}
+
+// ------------------------------------------------------ AA-pattern step ---
+// Single-buffer variant (FP64/FP32 storage).  Between library calls the state
+// keeps the pull layout of k_step, F[q][x] = f*_q(x) (post-collision values at
+// their own node).  A call first swaps every node's opposite pairs (layout S:
+// F[opp q][x] = f*_q(x)), then alternates
+//   odd step:  in_q(x) = F[opp q][x - xi_q] for a pore source, else F[q][x]
+//              (halfway bounce-back); closures, collision; f*_q(x) goes to
+//              F[q][x + xi_q] for a pore destination, else to F[opp q][x]
+//              (layout S -> I, I[q][x] = the value arriving at x in direction q);
+//   even step: in_q(x) = F[q][x]; closures, collision; f*_q(x) -> F[opp q][x]
+//              (layout I -> S);
+// and swaps the pairs back at the end (after an odd count, k_aa_unstream first
+// turns layout I into S).  Within a step every slot is read and then written by
+// one node only, so the update runs in place.  Values leaving through the z
+// faces are kept like bounced ones; the closures overwrite them.  The next
+// step's inlet density is formed exactly as in k_step: the landing rule of a
+// post-collision value does not depend on where it is stored.
+// LBM_AA_RELOAD_IDS: 1 = the gather-scatter step loads its 18 neighbour ids
+// again for the scatter (no spills at the 64-register cap), 0 = keeps them in
+// registers across the collision.
+#ifndef LBM_AA_RELOAD_IDS
+#define LBM_AA_RELOAD_IDS 1
+#endif
+
+// Row pointers of the single buffer as kernel parameters (constant bank), as
+// for k_step: no registers spent on 19 row addresses.
+template <class T>
+struct AAPtrs {
+    T* row[19];
+};
+
+template <class S, bool ODD>
+__global__ void __launch_bounds__(kBlock, step_min_blocks<S>())
+k_step_aa(const AAPtrs<typename S::T> F, int slot, DevLattice L, typename S::M sp, typename S::M sm,
+          BcState* bc, double* __restrict__ partials, unsigned* __restrict__ counter) {
+    static_assert(!S::kRef, "the AA pattern stores FP64 or FP32 values");
+    using M = typename S::M;
+    __shared__ double sh[32];
+    __shared__ bool last;
+    const int64_t i64 = (int64_t)blockIdx.x * kBlock + threadIdx.x;
+    const int i = (int)i64;
+    double part = 0.0;
+    if (i64 < L.n) {
+        M d[19];
+        int nb[19];  // odd step: pore id of x - xi_q (the pull source of q), or a negative marker
+        if constexpr (ODD) {
+            const uint64_t pol_idx = l2_policy_evict_last();
+            const uint32_t p = ld_index(L.vox + i, pol_idx);
+            d[0] = F.row[0][i];
+            for_q(std::make_integer_sequence<int, 18>{}, [&](auto qc) {
+                constexpr int Q = decltype(qc)::value + 1;
+                nb[Q] = ld_index(L.grid + (uint32_t)(p + (uint32_t)L.goff[Q]), pol_idx);
+                d[Q] = nb[Q] >= 0 ? F.row[opp(Q)][nb[Q]] : F.row[Q][i];
+            });
+        } else {
+            for_q(AllQ{}, [&](auto qc) {
+                constexpr int Q = decltype(qc)::value;
+                d[Q] = F.row[Q][i];
+            });
+        }
+        if (i < L.a_in) {
+            const M drin = bc->inlet_mode ? M(bc->drho_in_fixed) : M(bc->drho_in[slot]);
+            close_inlet(d, drin - inlet_known(d));
+        } else if (i64 >= L.n - L.a_out) {
+            close_outlet(d, outlet_known(d) - M(bc->drho_out));
+        }
+        collide(d, sp, sm);
+        // an opaque copy of i for the stores: sharing the load addresses would keep
+        // 19 64-bit addresses live across the collision
+        int j;
+        asm volatile("mov.b32 %0, %1;" : "=r"(j) : "r"(i));
+        if constexpr (ODD) {
+#if LBM_AA_RELOAD_IDS
+            // fresh policy and voxel index: nothing of the gather stays live
+            const uint64_t pol_s = l2_policy_evict_last();
+            const uint32_t ps = ld_index(L.vox + j, pol_s);
+#endif
+            F.row[0][j] = d[0];
+            for_q(std::make_integer_sequence<int, 18>{}, [&](auto qc) {
+                constexpr int Q = decltype(qc)::value + 1;
+                // x + xi_Q is the pull source of opp(Q)
+#if LBM_AA_RELOAD_IDS
+                const int dst = ld_index(L.grid + (uint32_t)(ps + (uint32_t)L.goff[opp(Q)]), pol_s);
+#else
+                const int dst = nb[opp(Q)];
+#endif
+                if (dst >= 0) F.row[Q][dst] = d[Q];
+                else F.row[opp(Q)][j] = d[Q];
+            });
+        } else {
+            for_q(AllQ{}, [&](auto qc) {
+                constexpr int Q = decltype(qc)::value;
+                F.row[opp(Q)][j] = d[Q];
+            });
+        }
+        if (i64 < L.a_01) part = next_inlet_part<S>(d, L, L.vox[i], i, M(0));
+    }
+    if ((int64_t)blockIdx.x * kBlock < L.a_01) {
+        const unsigned nbk = (unsigned)((L.a_01 + kBlock - 1) / kBlock);
+        const double b = block_sum<kBlock>(part, sh);
+        if (threadIdx.x == 0) {
+            partials[blockIdx.x] = b;
+            __threadfence();
+            last = atomicAdd(counter, 1u) == nbk - 1;
+        }
+        __syncthreads();
+        if (last) {
+            __threadfence();
+            double s = 0.0;
+            for (unsigned j = threadIdx.x; j < nbk; j += kBlock) s += __ldcg(partials + j);
+            s = block_sum<kBlock>(s, sh);
+            if (threadIdx.x == 0) {
+                bc->drho_in[slot ^ 1] = (bc->Q + s) / (double)L.a_in;
+                *counter = 0u;
+            }
+        }
+    }
+}
+
+// Pull layout <-> layout S: swap F[q][x] and F[opp q][x] at every node.
+template <class T>
+__global__ void k_aa_swap(T* __restrict__ f, int64_t n, int64_t ns) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+#pragma unroll
+    for (int q = 1; q < 19; q += 2) {  // opposite pairs are (q, q + 1), q odd
+        const T a = f[(int64_t)q * ns + i];
+        f[(int64_t)q * ns + i] = f[(int64_t)(q + 1) * ns + i];
+        f[(int64_t)(q + 1) * ns + i] = a;
+    }
+}
+
+// Layout I -> layout S after an odd step: the value that arrived at x in
+// direction q from the pore x - xi_q belongs in F[opp q][x - xi_q], and that
+// slot holds the value that arrived at x - xi_q in direction opp q from x,
+// which belongs in F[q][x]: one swap per pair, done by the node with odd q.
+// A value that arrived by bounce-back is already in place.
+template <class T>
+__global__ void k_aa_unstream(T* __restrict__ f, DevLattice L) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= L.n) return;
+    const uint32_t p = L.vox[i];
+#pragma unroll
+    for (int q = 1; q < 19; q += 2) {
+        const int id = __ldg(L.grid + (uint32_t)(p + (uint32_t)L.goff[q]));
+        if (id >= 0) {
+            T* a = f + (int64_t)q * L.ns + i;
+            T* b = f + (int64_t)(q + 1) * L.ns + id;
+            const T t = *a;
+            *a = *b;
+            *b = t;
         }
     }
 }
@@ -964,6 +1121,51 @@ cudaError_t launch_decode(int prec, const void* f, const DevLattice& L, const Bc
         using S = decltype(s);
         k_decode<S><<<blocks_for(L.n, 256), 256, 0, st>>>((const typename S::T*)f, L, bc, d);
         return cudaGetLastError();
+    });
+}
+
+cudaError_t launch_aa_step(int prec, void* f, int odd, int slot, const DevLattice& L, Relax r, BcState* bc,
+                           double* partials, unsigned* counter, cudaStream_t st) {
+    return dispatch(prec, [&](auto s) {
+        using S = decltype(s);
+        using M = typename S::M;
+        if constexpr (S::kRef) {
+            return cudaErrorInvalidValue;
+        } else {
+            AAPtrs<typename S::T> F;
+            for (int q = 0; q < 19; ++q) F.row[q] = (typename S::T*)f + (int64_t)q * L.ns;
+            if (odd)
+                k_step_aa<S, true><<<blocks_for(L.n, kBlock), kBlock, 0, st>>>(F, slot, L, (M)r.sp, (M)r.sm, bc,
+                                                                                partials, counter);
+            else
+                k_step_aa<S, false><<<blocks_for(L.n, kBlock), kBlock, 0, st>>>(F, slot, L, (M)r.sp, (M)r.sm, bc,
+                                                                                 partials, counter);
+            return cudaGetLastError();
+        }
+    });
+}
+
+cudaError_t launch_aa_swap(int prec, void* f, const DevLattice& L, cudaStream_t st) {
+    return dispatch(prec, [&](auto s) {
+        using S = decltype(s);
+        if constexpr (S::kRef) {
+            return cudaErrorInvalidValue;
+        } else {
+            k_aa_swap<typename S::T><<<blocks_for(L.n, 256), 256, 0, st>>>((typename S::T*)f, L.n, L.ns);
+            return cudaGetLastError();
+        }
+    });
+}
+
+cudaError_t launch_aa_unstream(int prec, void* f, const DevLattice& L, cudaStream_t st) {
+    return dispatch(prec, [&](auto s) {
+        using S = decltype(s);
+        if constexpr (S::kRef) {
+            return cudaErrorInvalidValue;
+        } else {
+            k_aa_unstream<typename S::T><<<blocks_for(L.n, 256), 256, 0, st>>>((typename S::T*)f, L);
+            return cudaGetLastError();
+        }
     });
 }
 

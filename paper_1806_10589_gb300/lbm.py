@@ -197,7 +197,8 @@ class Lattice:
         self._check(self._lib.lbm_set_pressure_bc(self._h, face, float(rho)))
 
     def set_kernel(self, variant):
-        """Step-kernel variant: 0 per-node, 1 pipelined 256-node tiles, 2 pipelined 128."""
+        """Step-kernel variant: 0 per-node (default), 1 pipelined 256-node tiles,
+        2 pipelined 128, 3 AA pattern (one buffer, FP64/FP32)."""
         self._check(self._lib.lbm_set_kernel(self._h, int(variant)))
 
     def step(self, n=1):

@@ -1,0 +1,113 @@
+"""GPU checks of the AA-pattern variant (lbm_set_kernel 3: one distribution
+buffer updated in place).
+
+* Parity: FP64 against the oracle (1e-11 relative, as the two-buffer path) for
+  even and odd step counts, graph-sized and ragged runs, both collision models.
+* Equivalence: FP32 and FP64 states and inlet densities equal those of the
+  two-buffer per-node kernel (the arithmetic per node is the same, so the
+  results agree to rounding of at most a few ulps; bit equality is expected).
+* Memory: entering the AA pattern releases the second buffer; leaving it
+  allocates it again, mid-run, without changing the trajectory.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from lbm_inputs import random_mask, sphere_pack, uniform_field
+
+pytestmark = pytest.mark.gpu
+EPS32 = float(np.finfo(np.float32).eps)
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+    import __graft_entry__
+
+    __graft_entry__.build()
+    return torch
+
+
+def _f0(mask, seed, amp=0.01):
+    return O.W[:, None, None, None] * (1.0 + amp * uniform_field((19,) + mask.shape, seed))
+
+
+def _run(mask, prec, variant, chunks, torch, tau=0.8, model="mrt", Q=0.002, seed=5):
+    from paper_1806_10589_gb300 import Lattice
+
+    with Lattice(mask, tau, model, prec, stream=torch.cuda.current_stream()) as lat:
+        lat.set_kernel(variant)
+        lat.set_flux_bc(Q)
+        lat.set_distributions(_f0(mask, seed))
+        for c in chunks:
+            lat.step(c)
+        return lat.distributions(), lat.get_flux(4), lat.get_flux(5)
+
+
+@pytest.mark.parametrize("steps", [1, 2, 15, 16])
+@pytest.mark.parametrize("model", ["mrt", "bgk"])
+def test_aa_fp64_matches_oracle(torch_cuda, steps, model):
+    m = random_mask(9, 8, 12, 0.3, 21)
+    got, (q_in, rho_in), _ = _run(m, "fp64", 3, [steps], torch_cuda, model=model)
+    ref = O.D3Q19Oracle(m, 0.8, model, Q=0.002)
+    ref.set_distributions(_f0(m, 5))
+    ref.step(steps)
+    assert np.abs(got - ref.f).max() <= 1e-11 * np.abs(ref.f).max()
+    assert abs(rho_in - ref.rho_in) <= 1e-12
+    assert abs(q_in - 0.002) <= 8 * int((m[0] == 0).sum()) * np.finfo(float).eps
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("chunks", [[130], [1, 64, 3], [65, 65]])
+def test_aa_equals_two_buffer_kernel(torch_cuda, prec, chunks):
+    """Graph-sized (64) and ragged chunks, odd and even call lengths."""
+    m = random_mask(37, 29, 21, 0.3, 8)
+    a, fa_in, fa_out = _run(m, prec, 0, chunks, torch_cuda)
+    b, fb_in, fb_out = _run(m, prec, 3, chunks, torch_cuda)
+    d = np.abs(a - b).max()
+    dev = np.abs(a - O.W[:, None, None, None] * (m == 0)).max()
+    tol = (4 * EPS32 * dev) if prec == "fp32" else 1e-14 * np.abs(a).max()
+    assert d <= tol, (d, "bit-equal" if d == 0 else "not bit-equal")
+    assert abs(fa_in[1] - fb_in[1]) <= (1e-6 if prec == "fp32" else 1e-13)
+    assert abs(fa_in[0] - fb_in[0]) <= (1e-6 if prec == "fp32" else 1e-13)
+    assert abs(fa_out[0] - fb_out[0]) <= (1e-6 if prec == "fp32" else 1e-13)
+
+
+def test_aa_switching_mid_run_releases_and_restores_memory(torch_cuda):
+    from paper_1806_10589_gb300 import Lattice
+
+    torch = torch_cuda
+    m, _ = sphere_pack(96, 6.0, 10.0, 0.4, seed=77, cache=False)
+    ref, _, _ = _run(m, "fp32", 0, [40], torch)
+    with Lattice(m, 0.8, "mrt", "fp32", stream=torch.cuda.current_stream()) as lat:
+        lat.set_flux_bc(0.002)
+        lat.set_distributions(_f0(m, 5))
+        n = lat.info()["n_pore"]
+        buf = 19 * ((n + 127) // 128 * 128) * 4
+        lat.step(7)
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        lat.set_kernel(3)
+        free1 = torch.cuda.mem_get_info()[0]
+        lat.step(21)
+        lat.set_kernel(0)
+        free2 = torch.cuda.mem_get_info()[0]
+        lat.step(12)
+        got = lat.distributions()
+    assert free1 - free0 >= buf - (2 << 20), (free0, free1, buf)
+    assert free1 - free2 >= buf - (2 << 20), (free1, free2, buf)
+    dev = np.abs(ref - O.W[:, None, None, None] * (m == 0)).max()
+    assert np.abs(got - ref).max() <= 4 * EPS32 * dev
+
+
+def test_aa_rejects_16bit_storage(torch_cuda):
+    from paper_1806_10589_gb300 import LBMError, Lattice
+
+    m = random_mask(8, 8, 8, 0.2, 1)
+    with Lattice(m, 0.8, "mrt", "fp16dev", stream=torch_cuda.cuda.current_stream()) as lat:
+        with pytest.raises(LBMError):
+            lat.set_kernel(3)
+        lat.step(2)  # still usable on its previous variant
