@@ -45,7 +45,10 @@ TAU = 0.7
 UBAR = 1e-4
 BYTES_PER_VALUE = {"fp64": 8, "fp32": 4, "fp16dev": 2, "bf16dev": 2}
 FALLBACK_HBM_GBS = 6800.0
-PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "k_step_fp32_sphere256.md")
+PROFILE_TRAFFIC = {0: os.path.join(ROOT, "profiles", "k_step_fp32_sphere256.md"),
+                   3: os.path.join(ROOT, "profiles", "k_step_aa_fp32_sphere256.md")}
+VARIANT_NAMES = {0: "per-node pull kernel, two buffers", 1: "cp.async-pipelined, 256-node tiles",
+                 2: "cp.async-pipelined, 128-node tiles", 3: "AA pattern, one buffer in place"}
 
 
 # --------------------------------------------------------------- helpers ---
@@ -90,12 +93,12 @@ def measured_hbm_peak():
     return FALLBACK_HBM_GBS, "fallback"
 
 
-def profiled_traffic(sha):
+def profiled_traffic(sha, variant=0):
     """dram bytes per launch of the step kernel from the committed ncu summary,
     if it was taken on the current kernel sources (else None)."""
     try:
-        txt = open(PROFILE_TRAFFIC).read()
-    except OSError:
+        txt = open(PROFILE_TRAFFIC[variant]).read()
+    except (OSError, KeyError):
         return None
     m_sha = re.search(r"kernel_sources_sha:\s*([0-9a-f]+)", txt)
     m_b = re.search(r"dram_bytes_per_launch_full_size:\s*([0-9.eE+]+)", txt)
@@ -387,7 +390,9 @@ def run_ours(args, rank, world, local):
     Q = UBAR * a_in
     prec = args.precision
     stream = torch.cuda.current_stream()
+    variant = args.variant if (args.variant != 3 or prec in ("fp32", "fp64")) else 0
     lat = Lattice(mask, TAU, "mrt", prec, stream=stream)
+    lat.set_kernel(variant)
     lat.set_flux_bc(Q)
     meta = lat.info()
     n = meta["n_pore"]
@@ -417,20 +422,31 @@ def run_ours(args, rank, world, local):
     q_in, rho_in = lat.get_flux(4)
 
     # dominant kernel: CUDA events around every launch, on the launching stream
-    k_prof = max(3, min(K, 400))
+    k_prof = max(4, min(K, 400)) // 2 * 2
     ms_step_k, ms_inlet_k = lat.time_kernels(k_prof)
     s = BYTES_PER_VALUE[prec]
     unit_bytes = 2 * 19 * s
     achieved = unit_bytes * n / (ms_step_k * 1e-3) / 1e9
     peak, peak_kind = measured_hbm_peak()
     sha = kernel_sources_sha()
-    traffic = profiled_traffic(sha) if prec == "fp32" else None
+    traffic = profiled_traffic(sha, variant) if prec == "fp32" else None
+    per_kernel = None
+    if variant == 3:
+        # the AA step alternates two launches (each one full step): time the
+        # gather-scatter launch alone (a 1-step call) and infer the node-local one
+        odd = sum(lat.time_kernels(1)[0] for _ in range(40)) / 40
+        even = max(2 * ms_step_k - odd, 1e-6)
+        per_kernel = {name: {"ms": round(t, 5), "achieved": round(unit_bytes * n / (t * 1e-3) / 1e9, 1),
+                             "frac": round(unit_bytes * n / (t * 1e-3) / 1e9 / peak, 4)}
+                      for name, t in (("k_step_aa<odd> (gather-scatter)", odd),
+                                      ("k_step_aa<even> (node-local)", even))}
     lat.close()
 
     # end to end through the public API with host buffers
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     with Lattice(mask, TAU, "mrt", prec, stream=stream) as lat2:
+        lat2.set_kernel(variant)
         lat2.set_flux_bc(Q)
         lat2.step(K)
         rho, ux, uy, uz = lat2.fields()
@@ -472,18 +488,23 @@ def run_ours(args, rank, world, local):
                                "6+6 reservoir layers), tau 0.7, u_mean 1e-4, %s storage" % (info["porosity"], prec),
                    "n_pore": n, "a_in": meta["a_in"], "box": [nx, ny, nz], "precision": prec,
                    "parallelism": "replicas" if world > 1 else "single",
-                   "l2": "inputs larger than L2 (two f buffers of %.0f MB each)" % (19 * s * n / 1e6),
+                   "step_variant": "%d: %s" % (variant, VARIANT_NAMES[variant]),
+                   "l2": "inputs larger than L2 (%s f buffer%s of %.0f MB)" % (
+                       "one" if variant == 3 else "two", "" if variant == 3 else "s", 19 * s * n / 1e6),
                    "device": dev_name},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": traffic,
-                     "kernel": "k_step", "kernel_ms": round(ms_step_k, 5),
+                     "kernel": "k_step_aa<odd/even> (alternating; each launch is one full step; "
+                               "pair mean)" if variant == 3 else "k_step",
+                     "kernel_ms": round(ms_step_k, 5), "per_kernel": per_kernel,
                      "bytes_per_unit": unit_bytes, "units_per_launch": n,
                      "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind
                      if peak_kind == "measured" else "fallback 6.8 TB/s"},
         "cpu_baseline": cpu,
         "e2e": {"value": round(e2e_mlups, 2), "unit": METRIC, "h2d_bytes_per_step": h2d / K,
                 "d2h_bytes_per_step": d2h / K},
-        "gpu_launches": K + (2 * (K // 1024) if prec in ("fp16dev", "bf16dev") else 0),
+        "gpu_launches": K + (2 * (K // 1024) if prec in ("fp16dev", "bf16dev") else 0)
+                        + ((2 + (K & 1)) if variant == 3 else 0),
         "time_to_steady": steady,
         "ensemble": ens,
         "two_fluid": two,
@@ -583,14 +604,15 @@ def run_profile_case(args):
 
     torch.cuda.set_device(0)
     mask, info, a_in = workload()
+    variant = args.variant if (args.variant != 3 or args.precision in ("fp32", "fp64")) else 0
     with Lattice(mask, TAU, "mrt", args.precision, stream=torch.cuda.current_stream()) as lat:
+        lat.set_kernel(variant)
         lat.set_flux_bc(UBAR * a_in)
         for _ in range(args.warmup):
             lat.step(1)
         ms_step, ms_in = lat.time_kernels(args.steps)
         n = lat.info()["n_pore"]
-    print(json.dumps({"profile_case": args.precision, "n_pore": n, "k_step_ms": ms_step,
-                      "k_inlet_reduce_ms": ms_in}))
+    print(json.dumps({"profile_case": args.precision, "variant": variant, "n_pore": n, "step_ms": ms_step}))
 
 
 def main(argv=None):
@@ -600,6 +622,8 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=200)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=list(BYTES_PER_VALUE), default="fp32")
+    ap.add_argument("--variant", type=int, choices=sorted(VARIANT_NAMES), default=3,
+                    help="step kernel (lbm_set_kernel); the AA pattern (3) falls back to 0 for 16-bit storage")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--steady", action=argparse.BooleanOptionalAction, default=True,
                     help="also run the time-to-steady-flux comparison (FP32 / FP16 / BF16)")

@@ -413,11 +413,11 @@ k_step(const StepPtrs<typename S::T> P, int slot, DevLattice L, typename S::M sp
 // faces are kept like bounced ones; the closures overwrite them.  The next
 // step's inlet density is formed exactly as in k_step: the landing rule of a
 // post-collision value does not depend on where it is stored.
-// LBM_AA_RELOAD_IDS: 1 = the gather-scatter step loads its 18 neighbour ids
-// again for the scatter (no spills at the 64-register cap), 0 = keeps them in
-// registers across the collision.
-#ifndef LBM_AA_RELOAD_IDS
-#define LBM_AA_RELOAD_IDS 1
+// Where the gather-scatter step keeps its 18 neighbour ids across the
+// collision (LBM_AA_IDS): 0 = registers (spills at the 64-register cap),
+// 1 = loads them again from the id grid, 2 = shared memory (18 KB per block).
+#ifndef LBM_AA_IDS
+#define LBM_AA_IDS 1
 #endif
 
 // Row pointers of the single buffer as kernel parameters (constant bank), as
@@ -427,14 +427,49 @@ struct AAPtrs {
     T* row[19];
 };
 
+// Resident blocks per SM the two AA kernels are compiled for (register caps).
+#ifndef LBM_AA_MIN_BLOCKS
+#define LBM_AA_MIN_BLOCKS 5
+#endif
+#ifndef LBM_AA_EVEN_MIN_BLOCKS
+#define LBM_AA_EVEN_MIN_BLOCKS 6
+#endif
+// LBM_AA_ID_HINT: 1 = the id grid is read with the L2 evict-last policy, 0 = plain.
+#ifndef LBM_AA_ID_HINT
+#define LBM_AA_ID_HINT 1
+#endif
 template <class S, bool ODD>
-__global__ void __launch_bounds__(kBlock, step_min_blocks<S>())
+constexpr int aa_min_blocks() {
+    return sizeof(typename S::M) == 8 ? 1 : (ODD ? LBM_AA_MIN_BLOCKS : LBM_AA_EVEN_MIN_BLOCKS);
+}
+template <class T>
+__device__ __forceinline__ T ld_aa_index(const T* a, uint64_t pol) {
+#if LBM_AA_ID_HINT
+    return ld_index(a, pol);
+#else
+    (void)pol;
+    return __ldg(a);
+#endif
+}
+__device__ __forceinline__ uint64_t aa_index_policy() {
+#if LBM_AA_ID_HINT
+    return l2_policy_evict_last();
+#else
+    return 0;
+#endif
+}
+
+template <class S, bool ODD>
+__global__ void __launch_bounds__(kBlock, aa_min_blocks<S, ODD>())
 k_step_aa(const AAPtrs<typename S::T> F, int slot, DevLattice L, typename S::M sp, typename S::M sm,
           BcState* bc, double* __restrict__ partials, unsigned* __restrict__ counter) {
     static_assert(!S::kRef, "the AA pattern stores FP64 or FP32 values");
     using M = typename S::M;
     __shared__ double sh[32];
     __shared__ bool last;
+#if LBM_AA_IDS == 2
+    __shared__ int sid[ODD ? 18 : 1][kBlock];
+#endif
     const int64_t i64 = (int64_t)blockIdx.x * kBlock + threadIdx.x;
     const int i = (int)i64;
     double part = 0.0;
@@ -442,12 +477,15 @@ k_step_aa(const AAPtrs<typename S::T> F, int slot, DevLattice L, typename S::M s
         M d[19];
         int nb[19];  // odd step: pore id of x - xi_q (the pull source of q), or a negative marker
         if constexpr (ODD) {
-            const uint64_t pol_idx = l2_policy_evict_last();
-            const uint32_t p = ld_index(L.vox + i, pol_idx);
+            const uint64_t pol_idx = aa_index_policy();
+            const uint32_t p = ld_aa_index(L.vox + i, pol_idx);
             d[0] = F.row[0][i];
             for_q(std::make_integer_sequence<int, 18>{}, [&](auto qc) {
                 constexpr int Q = decltype(qc)::value + 1;
-                nb[Q] = ld_index(L.grid + (uint32_t)(p + (uint32_t)L.goff[Q]), pol_idx);
+                nb[Q] = ld_aa_index(L.grid + (uint32_t)(p + (uint32_t)L.goff[Q]), pol_idx);
+#if LBM_AA_IDS == 2
+                sid[Q - 1][threadIdx.x] = nb[Q];
+#endif
                 d[Q] = nb[Q] >= 0 ? F.row[opp(Q)][nb[Q]] : F.row[Q][i];
             });
         } else {
@@ -468,17 +506,19 @@ k_step_aa(const AAPtrs<typename S::T> F, int slot, DevLattice L, typename S::M s
         int j;
         asm volatile("mov.b32 %0, %1;" : "=r"(j) : "r"(i));
         if constexpr (ODD) {
-#if LBM_AA_RELOAD_IDS
+#if LBM_AA_IDS == 1
             // fresh policy and voxel index: nothing of the gather stays live
-            const uint64_t pol_s = l2_policy_evict_last();
-            const uint32_t ps = ld_index(L.vox + j, pol_s);
+            const uint64_t pol_s = aa_index_policy();
+            const uint32_t ps = ld_aa_index(L.vox + j, pol_s);
 #endif
             F.row[0][j] = d[0];
             for_q(std::make_integer_sequence<int, 18>{}, [&](auto qc) {
                 constexpr int Q = decltype(qc)::value + 1;
                 // x + xi_Q is the pull source of opp(Q)
-#if LBM_AA_RELOAD_IDS
-                const int dst = ld_index(L.grid + (uint32_t)(ps + (uint32_t)L.goff[opp(Q)]), pol_s);
+#if LBM_AA_IDS == 1
+                const int dst = ld_aa_index(L.grid + (uint32_t)(ps + (uint32_t)L.goff[opp(Q)]), pol_s);
+#elif LBM_AA_IDS == 2
+                const int dst = sid[opp(Q) - 1][threadIdx.x];
 #else
                 const int dst = nb[opp(Q)];
 #endif
