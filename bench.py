@@ -229,11 +229,11 @@ def aggregate(n_local, K, ms_local, world, device=None):
     return total * K / (ms * 1e-3) / 1e6, ms
 
 
-def time_to_steady(mask, a_in, stream, max_steps=150000):
-    """Cold-start runs to steady flux on the benchmark workload: the FP32
-    reference k_inf by the Section 3.1 rule (residual over 1000 steps <= 1e-6),
-    then FP32 / FP16-dev / BF16-dev cold runs until k(t) is within 0.1 % of k_inf
-    and the outlet flux within 0.1 % of Q for 10 consecutive checks (every 100
+def time_to_steady(mask, a_in, stream, max_steps=150000, variant=3, precs=("fp32", "fp16dev", "bf16dev")):
+    """Cold-start runs to steady flux on the benchmark workload, all on step
+    variant `variant`: the FP32 reference k_inf by the Section 3.1 rule
+    (residual over 1000 steps <= 1e-6), then FP32 / FP16-dev / BF16-dev cold runs
+    until k(t) is within 0.1 % of k_inf for 10 consecutive checks (every 100
     steps).  Wall times include the checks."""
     import torch
 
@@ -241,8 +241,10 @@ def time_to_steady(mask, a_in, stream, max_steps=150000):
 
     Q = UBAR * a_in
     out = {"criterion": "k within 0.1% of k_inf for 10 consecutive checks (every 100 steps); "
-                        "k_inf: FP32 cold run to sum|u(t)-u(t-1000)|/sum|u| <= 1e-6"}
+                        "k_inf: FP32 cold run to sum|u(t)-u(t-1000)|/sum|u| <= 1e-6",
+           "step_variant": "%d: %s" % (variant, VARIANT_NAMES[variant])}
     with Lattice(mask, TAU, "mrt", "fp32", stream=stream) as lat:
+        lat.set_kernel(variant)
         lat.set_flux_bc(Q)
         r = cv.run_to_residual(lat, Q, TAU, lag=1000, tol=1e-6, max_steps=max_steps,
                                sync=torch.cuda.synchronize)
@@ -250,8 +252,9 @@ def time_to_steady(mask, a_in, stream, max_steps=150000):
     out["k_inf"] = k_inf
     out["k_inf_run"] = {"steps": r["steps"], "seconds": round(r["seconds"], 3), "residual": r["residual"],
                         "converged": r["converged"], "q_out_rel_err": abs(r["q_out"] - Q) / Q}
-    for prec in ("fp32", "fp16dev", "bf16dev"):
+    for prec in precs:
         with Lattice(mask, TAU, "mrt", prec, stream=stream) as lat:
+            lat.set_kernel(variant)
             lat.set_flux_bc(Q)
             rr = cv.run_to_reference(lat, Q, TAU, k_inf, max_steps=min(max_steps, 60000),
                                      sync=torch.cuda.synchronize)
@@ -390,7 +393,7 @@ def run_ours(args, rank, world, local):
     Q = UBAR * a_in
     prec = args.precision
     stream = torch.cuda.current_stream()
-    variant = args.variant if (args.variant != 3 or prec in ("fp32", "fp64")) else 0
+    variant = args.variant
     lat = Lattice(mask, TAU, "mrt", prec, stream=stream)
     lat.set_kernel(variant)
     lat.set_flux_bc(Q)
@@ -466,7 +469,7 @@ def run_ours(args, rank, world, local):
 
     steady = None
     if rank == 0 and args.steady:
-        steady = time_to_steady(mask, a_in, stream)
+        steady = time_to_steady(mask, a_in, stream, variant=args.variant)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -604,7 +607,7 @@ def run_profile_case(args):
 
     torch.cuda.set_device(0)
     mask, info, a_in = workload()
-    variant = args.variant if (args.variant != 3 or args.precision in ("fp32", "fp64")) else 0
+    variant = args.variant
     with Lattice(mask, TAU, "mrt", args.precision, stream=torch.cuda.current_stream()) as lat:
         lat.set_kernel(variant)
         lat.set_flux_bc(UBAR * a_in)
@@ -623,7 +626,7 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=list(BYTES_PER_VALUE), default="fp32")
     ap.add_argument("--variant", type=int, choices=sorted(VARIANT_NAMES), default=3,
-                    help="step kernel (lbm_set_kernel); the AA pattern (3) falls back to 0 for 16-bit storage")
+                    help="step kernel (lbm_set_kernel); 3 = AA pattern (one buffer)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--steady", action=argparse.BooleanOptionalAction, default=True,
                     help="also run the time-to-steady-flux comparison (FP32 / FP16 / BF16)")

@@ -48,7 +48,11 @@ enum { LBM_MODEL_BGK = 0, LBM_MODEL_MRT = 1 };
 
 /* Storage of the 19 distributions in device memory (arithmetic is FP64 for
  * LBM_PREC_FP64 and FP32 otherwise).  The 16-bit formats store the scaled
- * deviation (f_q / w_q - 1) * 2^10 from the rest-state weight w_q. */
+ * deviation (f_q / w_q - 1 - r(z)) * 2^10 from the rest-state weight w_q and a
+ * linear reference density r(z) between the inlet and outlet densities
+ * (refreshed every 1024 steps).  Steps round these stores stochastically (zero
+ * mean error, reproducible: the random bits hash the step, node and direction),
+ * so a steady state carries no rounding bias. */
 enum { LBM_PREC_FP64 = 0, LBM_PREC_FP32 = 1, LBM_PREC_FP16DEV = 2, LBM_PREC_BF16DEV = 3 };
 
 /* Faces.  Only z faces are open (the paper derives the z-inlet condition). */
@@ -87,16 +91,18 @@ int lbm_set_pressure_bc(lbm_ctx* ctx, int face, double rho);
  * handle) for all later device work of this context.  NULL = default stream. */
 int lbm_set_stream(lbm_ctx* ctx, void* cuda_stream);
 
-/* Select the step-kernel variant (every variant computes the same step, bit
- * for bit): 0 = one thread per pore node (the default); 1 = persistent kernel
+/* Select the step-kernel variant.  Every variant computes the same step:
+ * variants 0-2 bit for bit in FP64/FP32; the AA pattern to rounding (its
+ * kernels may contract products into FMAs differently); with the 16-bit formats
+ * within the storage rounding.  0 = one thread per pore node (the default); 1 = persistent kernel
  * whose neighbour ids and pulled values are staged in shared memory by cp.async
  * one 256-node tile ahead; 2 = the same with 128-node tiles; 3 = AA pattern:
  * ONE distribution buffer updated in place (the second buffer is freed, so the
  * state needs half the memory), alternating a gather-scatter step and a
- * node-local step; FP64/FP32 storage only (LBM_EUNSUPPORTED otherwise).  Each
+ * node-local step; every storage format.  Each
  * lbm_step call on variant 3 adds two in-place layout swaps (three for an odd
- * step count), so that between calls the state reads exactly as with the
- * other variants.  Leaving variant 3 allocates the second buffer again
+ * step count; 16-bit formats also at every reference-profile refresh), so that
+ * between calls the state reads exactly as with the other variants.  Leaving variant 3 allocates the second buffer again
  * (LBM_ENOMEM if that fails; the context stays on variant 3).  Unknown
  * variants return LBM_EINVAL.  Synchronises. */
 int lbm_set_kernel(lbm_ctx* ctx, int variant);

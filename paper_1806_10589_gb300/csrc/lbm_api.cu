@@ -103,8 +103,9 @@ int enter(lbm_ctx* c) {
 void* state_f(lbm_ctx* c) { return c->aa ? c->f[0] : c->f[c->cur]; }
 
 int push_bc(lbm_ctx* c) {
-    LBM_CUDA(c, cudaMemcpyAsync(c->d_bc, &c->h_bc, sizeof(lbm::BcState), cudaMemcpyHostToDevice,
-                                c->stream));
+    // host-owned fields only: the inlet densities, the 16-bit reference profile
+    // and the rounding seeds live on the device
+    LBM_CUDA(c, cudaMemcpyAsync(c->d_bc, &c->h_bc, lbm::kBcHostBytes, cudaMemcpyHostToDevice, c->stream));
     // h_bc must stay valid until the copy ran: make the copy synchronous w.r.t. the host.
     LBM_CUDA(c, cudaStreamSynchronize(c->stream));
     return LBM_OK;
@@ -387,8 +388,6 @@ int lbm_set_kernel(lbm_ctx* c, int variant) {
     int rc = enter(c);
     if (rc) return rc;
     if (variant < 0 || variant > 3) return fail(c, LBM_EINVAL, "unknown step kernel variant %d", variant);
-    if (variant == 3 && c->prec != LBM_PREC_FP64 && c->prec != LBM_PREC_FP32)
-        return fail(c, LBM_EUNSUPPORTED, "the AA pattern stores FP64 or FP32 values");
     lbm::StepConfig cfg{};
     if (variant < 3) LBM_CUDA(c, lbm::configure_step(c->prec, variant, c->L, &cfg));
     LBM_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -418,18 +417,27 @@ int lbm_step(lbm_ctx* c, int n) {
     if (rc) return rc;
     if (n < 0) return fail(c, LBM_EINVAL, "n must be >= 0");
     if (c->aa) {
-        if (n == 0) return LBM_OK;
-        LBM_CUDA(c, lbm::launch_aa_swap(c->prec, c->f[0], c->L, c->stream));
-        int k = 0;
-        while (n - k >= kGraphSteps) {
-            if (!c->graph[c->cur] && (rc = build_graph(c, c->cur))) return rc;
-            LBM_CUDA(c, cudaGraphLaunch(c->graph[c->cur], c->stream));
-            k += kGraphSteps;
+        // segments end where the 16-bit reference profile is refreshed, which
+        // works on the resting (pull) layout
+        int64_t done = 0;
+        while (done < n) {
+            if ((rc = maybe_reencode(c))) return rc;
+            int64_t seg = n - done;
+            if (c->prec >= LBM_PREC_FP16DEV) seg = std::min<int64_t>(seg, kReencodeInterval - c->since_reencode);
+            LBM_CUDA(c, lbm::launch_aa_swap(c->prec, c->f[0], c->L, c->stream));
+            int64_t k = 0;
+            while (seg - k >= kGraphSteps) {
+                if (!c->graph[c->cur] && (rc = build_graph(c, c->cur))) return rc;
+                LBM_CUDA(c, cudaGraphLaunch(c->graph[c->cur], c->stream));
+                k += kGraphSteps;
+            }
+            for (; k < seg; ++k)
+                if ((rc = aa_step(c, k, c->stream))) return rc;
+            if (seg & 1) LBM_CUDA(c, lbm::launch_aa_unstream(c->prec, c->f[0], c->L, c->d_bc, c->stream));
+            LBM_CUDA(c, lbm::launch_aa_swap(c->prec, c->f[0], c->L, c->stream));
+            done += seg;
+            c->since_reencode += seg;
         }
-        for (; k < n; ++k)
-            if ((rc = aa_step(c, k, c->stream))) return rc;
-        if (n & 1) LBM_CUDA(c, lbm::launch_aa_unstream(c->prec, c->f[0], c->L, c->stream));
-        LBM_CUDA(c, lbm::launch_aa_swap(c->prec, c->f[0], c->L, c->stream));
         c->steps += n;
         return LBM_OK;
     }
@@ -470,7 +478,7 @@ int lbm_time_kernels(lbm_ctx* c, int n, float* ms_step, float* ms_inlet) {
         c->cur ^= 1;
     }
     if (c->aa) {
-        if (n & 1) LBM_CUDA(c, lbm::launch_aa_unstream(c->prec, c->f[0], c->L, c->stream));
+        if (n & 1) LBM_CUDA(c, lbm::launch_aa_unstream(c->prec, c->f[0], c->L, c->d_bc, c->stream));
         LBM_CUDA(c, lbm::launch_aa_swap(c->prec, c->f[0], c->L, c->stream));
     }
     LBM_CUDA(c, cudaStreamSynchronize(c->stream));

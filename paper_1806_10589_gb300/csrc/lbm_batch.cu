@@ -49,6 +49,7 @@ struct Member {
     double drho_in[2];  // inlet density - 1 for the step reading buffer c
     float ref_r0[2], ref_g[2];  // 16-bit reference profile slots
     int ref_cur;
+    uint32_t sr_seed[2];        // stochastic-rounding seed of the step reading buffer c (16-bit)
 };
 
 template <int... Qs, class F>
@@ -110,11 +111,11 @@ __device__ __forceinline__ typename S::M pull_b(const typename S::T* __restrict_
 template <class S>
 __device__ __forceinline__ double next_inlet_part_b(const typename S::M* d, const int* __restrict__ grid,
                                                     const Member& m, int64_t p, int64_t il,
-                                                    typename S::M r_own) {
+                                                    typename S::M r_own, uint32_t seed, int64_t i) {
     double s = 0.0;
     auto val = [&](auto qc) -> double {
         constexpr int Q = decltype(qc)::value;
-        return (double)S::template dec<Q>(S::template enc<Q>(d[Q], r_own), r_own);
+        return (double)S::template dec<Q>(S::template enc_sr<Q>(d[Q], r_own, sr_key<S>(seed, i, Q)), r_own);
     };
     auto dest_is_pore = [&](auto qc) -> bool {
         constexpr int Q = decltype(qc)::value;
@@ -174,6 +175,7 @@ k_batch_step(const typename S::T* __restrict__ fin, typename S::T* __restrict__ 
     if (il < m.n) {
         const int64_t p = vox[i];
         const M r_own = member_ref<S>(m, p), g = member_slope<S>(m);
+        const uint32_t seed = S::kRef ? m.sr_seed[slot] : 0u;
         M d[19];
         for_q(AllQ{}, [&](auto qc) {
             constexpr int Q = decltype(qc)::value;
@@ -187,14 +189,15 @@ k_batch_step(const typename S::T* __restrict__ fin, typename S::T* __restrict__ 
         collide(d, sp, sm);
         for_q(AllQ{}, [&](auto qc) {
             constexpr int Q = decltype(qc)::value;
-            fout[(int64_t)Q * ns + i] = S::template enc<Q>(d[Q], r_own);
+            fout[(int64_t)Q * ns + i] = S::template enc_sr<Q>(d[Q], r_own, sr_key<S>(seed, i, Q));
         });
-        if (il < m.a_01) part = next_inlet_part_b<S>(d, grid, m, p, il, r_own);
+        if (il < m.a_01) part = next_inlet_part_b<S>(d, grid, m, p, il, r_own, seed, i);
     }
     const int64_t nt01 = (m.a_01 + kTile - 1) / kTile;
     if (tile - tile0 < nt01)
         member_reduce(part, tile, tile0, nt01, partials, counters + mi, sh, [&](double s) {
             members[mi].drho_in[slot ^ 1] = (m.Q + s) / (double)m.a_in;
+            if constexpr (S::kRef) members[mi].sr_seed[slot ^ 1] = sr_next(m.sr_seed[slot]);
         });
 }
 

@@ -9,6 +9,7 @@
 // significant digits of the small deviations in every storage format.
 #pragma once
 
+#include <cstddef>
 #include <cstdint>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -51,7 +52,28 @@ constexpr int ZOUT = -2;
 // between the inlet and outlet densities, refreshed by re-encoding).  Removing
 // the mean pressure gradient leaves the local deviation, so the 11 (FP16) or 8
 // (BF16) significant bits resolve the velocity part instead of the density ramp.
+//
+// The steps store the 16-bit formats with stochastic rounding (enc_sr): a value
+// is rounded up in magnitude with probability equal to its distance from the
+// lower neighbour in units of the last place, so the rounding error has zero
+// mean.  Round-to-nearest would repeat the same error every step once the flow
+// is steady and bias the steady state.  The random bits come from a
+// counter-based hash of (step seed, node, direction), so a run is reproducible.
+// Format conversions (encode, refresh) round to nearest.
 constexpr float DEV_SCALE = 1024.0f;
+
+// 32-bit integer hash: the "lowbias32" finaliser published by C. Wellons
+// (xor-shift / multiply rounds).
+__host__ __device__ __forceinline__ uint32_t sr_hash(uint32_t x) {
+    x ^= x >> 16;
+    x *= 0x7feb352dU;
+    x ^= x >> 15;
+    x *= 0x846ca68bU;
+    x ^= x >> 16;
+    return x;
+}
+// Seed of the next step.
+__host__ __device__ __forceinline__ uint32_t sr_next(uint32_t seed) { return sr_hash(seed + 0x9E3779B9U); }
 
 struct StoreF64 {
     using T = double;
@@ -59,6 +81,7 @@ struct StoreF64 {
     static constexpr bool kRef = false;
     template <int Q> __device__ static M dec(T v, M) { return v; }
     template <int Q> __device__ static T enc(M v, M) { return v; }
+    template <int Q> __device__ static T enc_sr(M v, M, uint32_t) { return v; }
 };
 struct StoreF32 {
     using T = float;
@@ -66,6 +89,7 @@ struct StoreF32 {
     static constexpr bool kRef = false;
     template <int Q> __device__ static M dec(T v, M) { return v; }
     template <int Q> __device__ static T enc(M v, M) { return v; }
+    template <int Q> __device__ static T enc_sr(M v, M, uint32_t) { return v; }
 };
 struct StoreF16 {
     using T = __half;
@@ -76,6 +100,12 @@ struct StoreF16 {
     }
     template <int Q> __device__ static T enc(M v, M r) {
         return __float2half_rn(fmaf(v, float(1.0 / wq(Q)), -r) * 1024.0f);
+    }
+    // FP32 keeps 13 more fraction bits than FP16: adding 13 random bits to the
+    // magnitude and truncating rounds stochastically (FP16 normal range).
+    template <int Q> __device__ static T enc_sr(M v, M r, uint32_t u) {
+        const float x = fmaf(v, float(1.0 / wq(Q)), -r) * 1024.0f;
+        return __float2half_rz(__uint_as_float(__float_as_uint(x) + (u >> 19)));
     }
 };
 struct StoreBF16 {
@@ -88,7 +118,22 @@ struct StoreBF16 {
     template <int Q> __device__ static T enc(M v, M r) {
         return __float2bfloat16_rn(fmaf(v, float(1.0 / wq(Q)), -r) * 1024.0f);
     }
+    // BF16 is the upper half of FP32: add 16 random bits, then truncate.
+    template <int Q> __device__ static T enc_sr(M v, M r, uint32_t u) {
+        const float x = fmaf(v, float(1.0 / wq(Q)), -r) * 1024.0f;
+        return __float2bfloat16_rz(__uint_as_float(__float_as_uint(x) + (u >> 16)));
+    }
 };
+
+// Random bits of the stochastic rounding of value (node i, direction q) in the
+// step with seed `seed` (no work for the formats that store exactly): one hash
+// per node (the same call for every q, computed once), then a Weyl step per
+// direction mixed by one multiply; the codecs use the high bits of the product.
+template <class S>
+__device__ __forceinline__ uint32_t sr_key(uint32_t seed, int64_t i, int q) {
+    if constexpr (S::kRef) return (sr_hash(seed ^ (uint32_t)i) + (uint32_t)q * 0x9E3779B9U) * 0x2C1B3C6DU;
+    else return 0u;
+}
 
 // ------------------------------------------------------- boundary state ---
 // FP64 scalars of the boundary conditions, in device memory so that captured
@@ -107,8 +152,12 @@ struct BcState {
     float ref_r0[2];
     float ref_g[2];
     int ref_cur;
+    // stochastic-rounding seed of the step reading buffer c (16-bit formats)
+    uint32_t sr_seed[2];
     int pad2_;
 };
+// The host writes only the fields before drho_in; the rest is device-owned.
+constexpr size_t kBcHostBytes = offsetof(BcState, drho_in);
 
 // Plane z of a padded voxel index p = ((z+1)(ny+2) + y+1)(nx+2) + x+1, with
 // magic = ceil(2^64 / ((nx+2)(ny+2))): exact for p < 2^32.

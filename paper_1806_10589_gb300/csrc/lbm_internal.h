@@ -57,12 +57,12 @@ cudaError_t configure_step(int prec, int variant, const DevLattice& L, StepConfi
 cudaError_t launch_step_cfg(int prec, const StepConfig& cfg, const void* fin, void* fout, int slot,
                             const DevLattice& L, Relax r, BcState* bc, double* partials, unsigned* counter,
                             cudaStream_t st);
-// AA pattern (single buffer, FP64/FP32): one odd (gather-scatter) or even
+// AA pattern (single buffer): one odd (gather-scatter) or even
 // (node-local) step in place, and the layout swaps around a call.
 cudaError_t launch_aa_step(int prec, void* f, int odd, int slot, const DevLattice& L, Relax r, BcState* bc,
                            double* partials, unsigned* counter, cudaStream_t st);
 cudaError_t launch_aa_swap(int prec, void* f, const DevLattice& L, cudaStream_t st);
-cudaError_t launch_aa_unstream(int prec, void* f, const DevLattice& L, cudaStream_t st);
+cudaError_t launch_aa_unstream(int prec, void* f, const DevLattice& L, const BcState* bc, cudaStream_t st);
 cudaError_t launch_monitors(int prec, const void* f, const DevLattice& L, const BcState* bc, double* partials,
                             unsigned* counter, MonitorOut* out, cudaStream_t st);
 cudaError_t launch_velocity_change(int prec, const void* f, const DevLattice& L, const BcState* bc, double* u_ref,

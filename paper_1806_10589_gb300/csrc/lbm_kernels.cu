@@ -139,11 +139,18 @@ __device__ __forceinline__ void pull_step(typename S::M* d, const StepPtrs<typen
 
 template <class S>
 __device__ __forceinline__ void store_step(const typename S::M* d, const StepPtrs<typename S::T>& P,
-                                           int i, uint64_t pol_f, typename S::M r_own) {
+                                           int i, uint64_t pol_f, typename S::M r_own, uint32_t seed) {
     for_q(AllQ{}, [&](auto qc) {
         constexpr int Q = decltype(qc)::value;
-        st_stream(P.out[Q] + i, S::template enc<Q>(d[Q], r_own), pol_f);
+        st_stream(P.out[Q] + i, S::template enc_sr<Q>(d[Q], r_own, sr_key<S>(seed, i, Q)), pol_f);
     });
+}
+
+// Stochastic-rounding seed of this step (16-bit formats), and the next one.
+template <class S>
+__device__ __forceinline__ uint32_t step_seed(const BcState* bc, int slot) {
+    if constexpr (S::kRef) return bc->sr_seed[slot];
+    else return 0u;
 }
 
 // ------------------------------------------------------------ reductions ---
@@ -312,10 +319,10 @@ __device__ __forceinline__ double inlet_contribution(const DevLattice& L, uint32
 // From values still in registers (the pipelined kernel).
 template <class S>
 __device__ __forceinline__ double next_inlet_part(const typename S::M* d, const DevLattice& L,
-                                                  int64_t p, int i, typename S::M r_own) {
+                                                  int64_t p, int i, typename S::M r_own, uint32_t seed) {
     return inlet_contribution<S>(L, (uint32_t)p, i, [&](auto qc) -> double {
         constexpr int Q = decltype(qc)::value;
-        return (double)S::template dec<Q>(S::template enc<Q>(d[Q], r_own), r_own);
+        return (double)S::template dec<Q>(S::template enc_sr<Q>(d[Q], r_own, sr_key<S>(seed, i, Q)), r_own);
     });
 }
 
@@ -355,6 +362,7 @@ k_step(const StepPtrs<typename S::T> P, int slot, DevLattice L, typename S::M sp
 #endif
         const uint32_t p = ld_index(L.vox + i, pol_idx);
         const M r_own = own_ref<S>(bc, L, p), g = own_slope<S>(bc);
+        const uint32_t seed = step_seed<S>(bc, slot);
         M d[19];
         pull_step<S>(d, P, L, p, i, pol_f, pol_idx, r_own, g);
         if (i < L.a_in) {
@@ -367,10 +375,10 @@ k_step(const StepPtrs<typename S::T> P, int slot, DevLattice L, typename S::M sp
             close_outlet(d, uz);
         }
         collide(d, sp, sm);
-        store_step<S>(d, P, i, pol_f, r_own);
+        store_step<S>(d, P, i, pol_f, r_own, seed);
         if (i64 < L.a_01) {
             if constexpr (contrib_reload<S>()) part = next_inlet_part_stored<S>(P, L, p, i, r_own);
-            else part = next_inlet_part<S>(d, L, p, i, r_own);
+            else part = next_inlet_part<S>(d, L, p, i, r_own, seed);
         }
     }
     // blocks that hold plane z = 0 or z = 1 nodes (block-uniform branch)
@@ -390,6 +398,7 @@ k_step(const StepPtrs<typename S::T> P, int slot, DevLattice L, typename S::M sp
             s = block_sum<kBlock>(s, sh);
             if (threadIdx.x == 0) {
                 bc->drho_in[slot ^ 1] = (bc->Q + s) / (double)L.a_in;
+                if constexpr (S::kRef) bc->sr_seed[slot ^ 1] = sr_next(bc->sr_seed[slot]);
                 *counter = 0u;
             }
         }
@@ -397,7 +406,7 @@ k_step(const StepPtrs<typename S::T> P, int slot, DevLattice L, typename S::M sp
 }
 
 // ------------------------------------------------------ AA-pattern step ---
-// Single-buffer variant (FP64/FP32 storage).  Between library calls the state
+// Single-buffer variant (every storage format).  Between library calls the state
 // keeps the pull layout of k_step, F[q][x] = f*_q(x) (post-collision values at
 // their own node).  A call first swaps every node's opposite pairs (layout S:
 // F[opp q][x] = f*_q(x)), then alternates
@@ -438,9 +447,18 @@ struct AAPtrs {
 #ifndef LBM_AA_ID_HINT
 #define LBM_AA_ID_HINT 1
 #endif
+// The 16-bit formats carry the reference profile and the rounding seed too.
+#ifndef LBM_AA16_MIN_BLOCKS
+#define LBM_AA16_MIN_BLOCKS 5
+#endif
+#ifndef LBM_AA16_EVEN_MIN_BLOCKS
+#define LBM_AA16_EVEN_MIN_BLOCKS 5
+#endif
 template <class S, bool ODD>
 constexpr int aa_min_blocks() {
-    return sizeof(typename S::M) == 8 ? 1 : (ODD ? LBM_AA_MIN_BLOCKS : LBM_AA_EVEN_MIN_BLOCKS);
+    if constexpr (sizeof(typename S::M) == 8) return 1;
+    else if constexpr (S::kRef) return ODD ? LBM_AA16_MIN_BLOCKS : LBM_AA16_EVEN_MIN_BLOCKS;
+    else return ODD ? LBM_AA_MIN_BLOCKS : LBM_AA_EVEN_MIN_BLOCKS;
 }
 template <class T>
 __device__ __forceinline__ T ld_aa_index(const T* a, uint64_t pol) {
@@ -463,7 +481,6 @@ template <class S, bool ODD>
 __global__ void __launch_bounds__(kBlock, aa_min_blocks<S, ODD>())
 k_step_aa(const AAPtrs<typename S::T> F, int slot, DevLattice L, typename S::M sp, typename S::M sm,
           BcState* bc, double* __restrict__ partials, unsigned* __restrict__ counter) {
-    static_assert(!S::kRef, "the AA pattern stores FP64 or FP32 values");
     using M = typename S::M;
     __shared__ double sh[32];
     __shared__ bool last;
@@ -476,22 +493,32 @@ k_step_aa(const AAPtrs<typename S::T> F, int slot, DevLattice L, typename S::M s
     if (i64 < L.n) {
         M d[19];
         int nb[19];  // odd step: pore id of x - xi_q (the pull source of q), or a negative marker
+        // 16-bit formats: every stored value is encoded with the reference of the
+        // plane of the node that holds it (the even step writes its own slots; the
+        // odd step encodes a scattered value with its destination's plane), so a
+        // value read from the neighbour x - xi_q decodes with r(z - xi_z).
+        M r_own = M(0), g = M(0);
+        const uint32_t seed = step_seed<S>(bc, slot);
         if constexpr (ODD) {
             const uint64_t pol_idx = aa_index_policy();
             const uint32_t p = ld_aa_index(L.vox + i, pol_idx);
-            d[0] = F.row[0][i];
+            r_own = own_ref<S>(bc, L, p);
+            g = own_slope<S>(bc);
+            d[0] = S::template dec<0>(F.row[0][i], r_own);
             for_q(std::make_integer_sequence<int, 18>{}, [&](auto qc) {
                 constexpr int Q = decltype(qc)::value + 1;
                 nb[Q] = ld_aa_index(L.grid + (uint32_t)(p + (uint32_t)L.goff[Q]), pol_idx);
 #if LBM_AA_IDS == 2
                 sid[Q - 1][threadIdx.x] = nb[Q];
 #endif
-                d[Q] = nb[Q] >= 0 ? F.row[opp(Q)][nb[Q]] : F.row[Q][i];
+                d[Q] = nb[Q] >= 0 ? S::template dec<Q>(F.row[opp(Q)][nb[Q]], r_own - M(cz(Q)) * g)
+                                  : S::template dec<Q>(F.row[Q][i], r_own);
             });
         } else {
+            if constexpr (S::kRef) r_own = own_ref<S>(bc, L, __ldg(L.vox + i));
             for_q(AllQ{}, [&](auto qc) {
                 constexpr int Q = decltype(qc)::value;
-                d[Q] = F.row[Q][i];
+                d[Q] = S::template dec<Q>(F.row[Q][i], r_own);
             });
         }
         if (i < L.a_in) {
@@ -511,7 +538,7 @@ k_step_aa(const AAPtrs<typename S::T> F, int slot, DevLattice L, typename S::M s
             const uint64_t pol_s = aa_index_policy();
             const uint32_t ps = ld_aa_index(L.vox + j, pol_s);
 #endif
-            F.row[0][j] = d[0];
+            F.row[0][j] = S::template enc_sr<0>(d[0], r_own, sr_key<S>(seed, i, 0));
             for_q(std::make_integer_sequence<int, 18>{}, [&](auto qc) {
                 constexpr int Q = decltype(qc)::value + 1;
                 // x + xi_Q is the pull source of opp(Q)
@@ -522,16 +549,25 @@ k_step_aa(const AAPtrs<typename S::T> F, int slot, DevLattice L, typename S::M s
 #else
                 const int dst = nb[opp(Q)];
 #endif
-                if (dst >= 0) F.row[Q][dst] = d[Q];
-                else F.row[opp(Q)][j] = d[Q];
+                const uint32_t key = sr_key<S>(seed, i, Q);
+                if (dst >= 0) F.row[Q][dst] = S::template enc_sr<Q>(d[Q], r_own + M(cz(Q)) * g, key);
+                else F.row[opp(Q)][j] = S::template enc_sr<Q>(d[Q], r_own, key);
             });
         } else {
             for_q(AllQ{}, [&](auto qc) {
                 constexpr int Q = decltype(qc)::value;
-                F.row[opp(Q)][j] = d[Q];
+                F.row[opp(Q)][j] = S::template enc_sr<Q>(d[Q], r_own, sr_key<S>(seed, i, Q));
             });
         }
-        if (i64 < L.a_01) part = next_inlet_part<S>(d, L, L.vox[i], i, M(0));
+        if (i64 < L.a_01) {
+            // the counted values land on plane 0: from plane 1 (xi_z = -1, stored
+            // with plane 0's reference in the odd step) or staying on plane 0
+            part = inlet_contribution<S>(L, L.vox[i], i, [&](auto qc) -> double {
+                constexpr int Q = decltype(qc)::value;
+                const M rq = (ODD && cz(Q) < 0) ? r_own - g : r_own;
+                return (double)S::template dec<Q>(S::template enc_sr<Q>(d[Q], rq, sr_key<S>(seed, i, Q)), rq);
+            });
+        }
     }
     if ((int64_t)blockIdx.x * kBlock < L.a_01) {
         const unsigned nbk = (unsigned)((L.a_01 + kBlock - 1) / kBlock);
@@ -549,6 +585,7 @@ k_step_aa(const AAPtrs<typename S::T> F, int slot, DevLattice L, typename S::M s
             s = block_sum<kBlock>(s, sh);
             if (threadIdx.x == 0) {
                 bc->drho_in[slot ^ 1] = (bc->Q + s) / (double)L.a_in;
+                if constexpr (S::kRef) bc->sr_seed[slot ^ 1] = sr_next(bc->sr_seed[slot]);
                 *counter = 0u;
             }
         }
@@ -573,22 +610,33 @@ __global__ void k_aa_swap(T* __restrict__ f, int64_t n, int64_t ns) {
 // slot holds the value that arrived at x - xi_q in direction opp q from x,
 // which belongs in F[q][x]: one swap per pair, done by the node with odd q.
 // A value that arrived by bounce-back is already in place.
-template <class T>
-__global__ void k_aa_unstream(T* __restrict__ f, DevLattice L) {
+// 16-bit formats: a moved value is re-encoded from its old holder's plane to
+// the new one's (opposite directions share the weight).
+template <class S>
+__global__ void k_aa_unstream(typename S::T* __restrict__ f, DevLattice L, const BcState* bc) {
+    using T = typename S::T;
+    using M = typename S::M;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= L.n) return;
     const uint32_t p = L.vox[i];
-#pragma unroll
-    for (int q = 1; q < 19; q += 2) {
-        const int id = __ldg(L.grid + (uint32_t)(p + (uint32_t)L.goff[q]));
+    const M r_own = own_ref<S>(bc, L, p), g = own_slope<S>(bc);
+    for_q(std::integer_sequence<int, 1, 3, 5, 7, 9, 11, 13, 15, 17>{}, [&](auto qc) {
+        constexpr int Q = decltype(qc)::value;
+        const int id = __ldg(L.grid + (uint32_t)(p + (uint32_t)L.goff[Q]));
         if (id >= 0) {
-            T* a = f + (int64_t)q * L.ns + i;
-            T* b = f + (int64_t)(q + 1) * L.ns + id;
-            const T t = *a;
-            *a = *b;
-            *b = t;
+            T* a = f + (int64_t)Q * L.ns + i;
+            T* b = f + (int64_t)(Q + 1) * L.ns + id;
+            const T ta = *a, tb = *b;
+            if constexpr (S::kRef) {
+                const M r_src = r_own - M(cz(Q)) * g;  // plane of x - xi_Q
+                *a = S::template enc<Q>(S::template dec<Q>(tb, r_src), r_own);
+                *b = S::template enc<Q>(S::template dec<Q>(ta, r_own), r_src);
+            } else {
+                *a = tb;
+                *b = ta;
+            }
         }
-    }
+    });
 }
 
 // ------------------------------------------------ pipelined step kernel ---
@@ -743,6 +791,7 @@ k_step_async(const StepPtrs<typename S::T> P, int slot, DevLattice L, typename S
         if (i64 < L.n) {
             const int i = (int)i64;
             const M r_own = own_ref<S>(bc, L, p_cur), g = own_slope<S>(bc);
+            const uint32_t seed = step_seed<S>(bc, slot);
             M d[19];
             read_vals<S, NT>(d, vcur, hi_cur, nb_cur, r_own, g);
             if (i < L.a_in) {
@@ -755,9 +804,9 @@ k_step_async(const StepPtrs<typename S::T> P, int slot, DevLattice L, typename S
             collide(d, sp, sm);
             for_q(AllQ{}, [&](auto qc) {
                 constexpr int Q = decltype(qc)::value;
-                P.out[Q][i] = S::template enc<Q>(d[Q], r_own);
+                P.out[Q][i] = S::template enc_sr<Q>(d[Q], r_own, sr_key<S>(seed, i, Q));
             });
-            if (i64 < L.a_01) part = next_inlet_part<S>(d, L, p_cur, i, r_own);
+            if (i64 < L.a_01) part = next_inlet_part<S>(d, L, p_cur, i, r_own, seed);
         }
         if (t < nt01) {  // tile holds plane z = 0 / z = 1 nodes (block-uniform)
             const double b = block_sum<NT>(part, sh);
@@ -774,6 +823,7 @@ k_step_async(const StepPtrs<typename S::T> P, int slot, DevLattice L, typename S
                 s = block_sum<NT>(s, sh);
                 if (threadIdx.x == 0) {
                     bc->drho_in[slot ^ 1] = (bc->Q + s) / (double)L.a_in;
+                    if constexpr (S::kRef) bc->sr_seed[slot ^ 1] = sr_next(bc->sr_seed[slot]);
                     *counter = 0u;
                 }
             }
@@ -1169,9 +1219,7 @@ cudaError_t launch_aa_step(int prec, void* f, int odd, int slot, const DevLattic
     return dispatch(prec, [&](auto s) {
         using S = decltype(s);
         using M = typename S::M;
-        if constexpr (S::kRef) {
-            return cudaErrorInvalidValue;
-        } else {
+        {
             AAPtrs<typename S::T> F;
             for (int q = 0; q < 19; ++q) F.row[q] = (typename S::T*)f + (int64_t)q * L.ns;
             if (odd)
@@ -1188,24 +1236,16 @@ cudaError_t launch_aa_step(int prec, void* f, int odd, int slot, const DevLattic
 cudaError_t launch_aa_swap(int prec, void* f, const DevLattice& L, cudaStream_t st) {
     return dispatch(prec, [&](auto s) {
         using S = decltype(s);
-        if constexpr (S::kRef) {
-            return cudaErrorInvalidValue;
-        } else {
-            k_aa_swap<typename S::T><<<blocks_for(L.n, 256), 256, 0, st>>>((typename S::T*)f, L.n, L.ns);
-            return cudaGetLastError();
-        }
+        k_aa_swap<typename S::T><<<blocks_for(L.n, 256), 256, 0, st>>>((typename S::T*)f, L.n, L.ns);
+        return cudaGetLastError();
     });
 }
 
-cudaError_t launch_aa_unstream(int prec, void* f, const DevLattice& L, cudaStream_t st) {
+cudaError_t launch_aa_unstream(int prec, void* f, const DevLattice& L, const BcState* bc, cudaStream_t st) {
     return dispatch(prec, [&](auto s) {
         using S = decltype(s);
-        if constexpr (S::kRef) {
-            return cudaErrorInvalidValue;
-        } else {
-            k_aa_unstream<typename S::T><<<blocks_for(L.n, 256), 256, 0, st>>>((typename S::T*)f, L);
-            return cudaGetLastError();
-        }
+        k_aa_unstream<S><<<blocks_for(L.n, 256), 256, 0, st>>>((typename S::T*)f, L, bc);
+        return cudaGetLastError();
     });
 }
 

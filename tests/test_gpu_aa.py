@@ -4,10 +4,14 @@ buffer updated in place).
 * Parity: FP64 against the oracle (1e-11 relative, as the two-buffer path) for
   even and odd step counts, graph-sized and ragged runs, both collision models.
 * Equivalence: FP32 and FP64 states and inlet densities equal those of the
-  two-buffer per-node kernel (the arithmetic per node is the same, so the
-  results agree to rounding of at most a few ulps; bit equality is expected).
+  two-buffer per-node kernel to rounding.  The formulas are the same, but the
+  compiler contracts some products into FMAs differently in the two kernels, so
+  a step can differ by an ulp of the largest deviation, and such differences
+  propagate like rounding errors: max|delta| <= N eps max|d| after N steps.
 * Memory: entering the AA pattern releases the second buffer; leaving it
   allocates it again, mid-run, without changing the trajectory.
+* 16-bit deviation storage on the AA pattern: oracle bound and a crossing of
+  the reference-profile refresh.
 """
 import numpy as np
 import pytest
@@ -69,7 +73,8 @@ def test_aa_equals_two_buffer_kernel(torch_cuda, prec, chunks):
     b, fb_in, fb_out = _run(m, prec, 3, chunks, torch_cuda)
     d = np.abs(a - b).max()
     dev = np.abs(a - O.W[:, None, None, None] * (m == 0)).max()
-    tol = (4 * EPS32 * dev) if prec == "fp32" else 1e-14 * np.abs(a).max()
+    N = sum(chunks)
+    tol = (N * EPS32 * dev) if prec == "fp32" else 1e-14 * np.abs(a).max()
     assert d <= tol, (d, "bit-equal" if d == 0 else "not bit-equal")
     assert abs(fa_in[1] - fb_in[1]) <= (1e-6 if prec == "fp32" else 1e-13)
     assert abs(fa_in[0] - fb_in[0]) <= (1e-6 if prec == "fp32" else 1e-13)
@@ -100,14 +105,51 @@ def test_aa_switching_mid_run_releases_and_restores_memory(torch_cuda):
     assert free1 - free0 >= buf - (2 << 20), (free0, free1, buf)
     assert free1 - free2 >= buf - (2 << 20), (free1, free2, buf)
     dev = np.abs(ref - O.W[:, None, None, None] * (m == 0)).max()
-    assert np.abs(got - ref).max() <= 4 * EPS32 * dev
+    assert np.abs(got - ref).max() <= 40 * EPS32 * dev
 
 
-def test_aa_rejects_16bit_storage(torch_cuda):
-    from paper_1806_10589_gb300 import LBMError, Lattice
+@pytest.mark.parametrize("prec,bits", [("fp16dev", 11), ("bf16dev", 8)])
+@pytest.mark.parametrize("chunks", [[10], [3, 4]])
+def test_aa_16bit_matches_oracle(torch_cuda, prec, bits, chunks):
+    """16-bit deviation storage on the AA pattern (scattered values encoded with
+    the destination plane's reference; an odd call re-encodes in the un-stream
+    swap): within the stochastic-rounding bound of the two-buffer path,
+    8 N 2^-p max|d| after N steps."""
+    m = random_mask(13, 11, 10, 0.3, 3)
+    N = sum(chunks)
+    got, _, _ = _run(m, prec, 3, chunks, torch_cuda, seed=7)
+    ref = O.D3Q19Oracle(m, 0.8, "mrt", Q=0.002)
+    ref.set_distributions(_f0(m, 7))
+    ref.step(N)
+    d_ref = ref.f - O.W[:, None, None, None] * (m == 0)
+    assert np.isfinite(got).all()
+    assert np.abs(got - ref.f).max() <= 8 * N * 2.0 ** -bits * np.abs(d_ref).max()
 
-    m = random_mask(8, 8, 8, 0.2, 1)
-    with Lattice(m, 0.8, "mrt", "fp16dev", stream=torch_cuda.cuda.current_stream()) as lat:
-        with pytest.raises(LBMError):
-            lat.set_kernel(3)
-        lat.step(2)  # still usable on its previous variant
+
+@pytest.mark.parametrize("prec", ["fp16dev", "bf16dev"])
+def test_aa_16bit_crosses_reference_refresh(torch_cuda, prec):
+    """1100 steps on the AA pattern cross a refresh of the 16-bit reference
+    profile (every 1024 steps, done between segments in the resting layout):
+    the flux stays exact to the storage rounding and the state stays close to
+    the FP32 run, as for the two-buffer path."""
+    from paper_1806_10589_gb300 import Lattice
+    from lbm_inputs import duct_mask
+
+    m = duct_mask(10, 9, 40)
+    Q = 2e-3 * int((m[0] == 0).sum())
+    res = {}
+    for p, v in (("fp32", 0), (prec, 3)):
+        with Lattice(m, 0.8, "mrt", p, stream=torch_cuda.cuda.current_stream()) as lat:
+            lat.set_kernel(v)
+            lat.set_flux_bc(Q)
+            lat.step(700)
+            lat.step(401)
+            q_in, rho_in = lat.get_flux(4)
+            res[p] = (lat.fields(), q_in, rho_in)
+    (rho32, _, _, uz32), _, rin32 = res["fp32"]
+    (rho16, _, _, uz16), q16, rin16 = res[prec]
+    bits = 11 if prec == "fp16dev" else 8
+    dmax = float(np.abs(rho32[m == 0] - 1).max())
+    assert abs(q16 - Q) <= 64 * 2.0 ** -bits * dmax * int((m[0] == 0).sum()) / 19
+    assert np.abs(uz16 - uz32).max() <= 0.2 * np.abs(uz32).max() * (2.0 ** (11 - bits))
+    assert abs(rin16 - rin32) <= 0.05 * abs(rin32 - 1)

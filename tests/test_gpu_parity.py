@@ -7,8 +7,10 @@ Tolerances (written here, derived in the design notes):
   * FP32 (stores d = f - w, FP32 arithmetic): per step each value picks up a few
     ulps of the largest deviation it is formed from, so after N steps
     max |delta f| <= 20 * N * eps32 * max |d|  (d = f - w).
-  * FP16/BF16 deviation storage: every store rounds d/w * 2^10 to 11 (FP16) or 8
-    (BF16) significant bits; the bound is 4 * N * 2^-p * max |d|.
+  * FP16/BF16 deviation storage: every store rounds d/w * 2^10 stochastically to
+    11 (FP16) or 8 (BF16) significant bits, an error below one unit in the last
+    place (2^(1-p) relative, twice the round-to-nearest bound); the bound is
+    8 * N * 2^-p * max |d|.
 """
 import math
 
@@ -197,7 +199,7 @@ def test_16bit_deviation_storage_error(torch_cuda, prec, bits):
     got, ref, _, _ = _run_pair(m, 0.8, "mrt", prec, N, torch_cuda, seed=7)
     d_ref = ref.f - O.W[:, None, None, None] * (m == 0)
     err = np.abs(got - ref.f).max()
-    bound = 4 * N * 2.0 ** -bits * np.abs(d_ref).max()
+    bound = 8 * N * 2.0 ** -bits * np.abs(d_ref).max()
     assert np.isfinite(got).all()
     assert err <= bound, (err, bound)
 
@@ -302,7 +304,7 @@ def test_step_variants_reduced_precision(torch_cuda, variant, prec, bound_bits):
     if bound_bits is None:
         bound = 20 * N * EPS32 * np.abs(d_ref).max()
     else:
-        bound = 4 * N * 2.0 ** -bound_bits * np.abs(d_ref).max()
+        bound = 8 * N * 2.0 ** -bound_bits * np.abs(d_ref).max()
     assert err <= bound, (err, bound)
 
 
@@ -336,3 +338,14 @@ def test_16bit_reference_refresh_keeps_state_and_flux(torch_cuda, prec):
     assert abs(q16 - Q) <= 64 * 2.0 ** -bits * dmax * int((m[0] == 0).sum()) / 19
     assert np.abs(uz16 - uz32).max() <= 0.2 * np.abs(uz32).max() * (2.0 ** (11 - bits))
     assert abs(rin16 - rin32) <= 0.05 * abs(rin32 - 1)
+
+
+@pytest.mark.parametrize("prec", ["fp16dev", "bf16dev"])
+def test_16bit_stochastic_rounding_is_reproducible(torch_cuda, prec):
+    """The rounding bits come from a counter-based hash of (step seed, node,
+    direction): two identical runs give identical states, and changing only the
+    step count changes them."""
+    m = random_mask(17, 13, 15, 0.3, 4)
+    a = _run_variant(m, 0.8, prec, 70, 0, torch_cuda, seed=5)[1]
+    b = _run_variant(m, 0.8, prec, 70, 0, torch_cuda, seed=5)[1]
+    np.testing.assert_array_equal(a, b)
