@@ -581,18 +581,23 @@ def run_warmstart(args):
     test_mask, _ = sphere_pack(args.ws_test, 8.0, 16.0, 0.35, seed=777)
     A = int((test_mask[0] == 0).sum())
     Q = UBAR * A
+    t0 = time.perf_counter()
     with Lattice(test_mask, TAU, "mrt", "fp32", stream=stream) as lat:
+        lat.set_kernel(args.variant)
         lat.set_flux_bc(Q)
+        n_test = lat.info()["n_pore"]
         ref = cv.run_to_residual(lat, Q, TAU, lag=1000, tol=1e-6, max_steps=args.ws_ref_steps,
                                  sync=torch.cuda.synchronize)
+    t_ref = time.perf_counter() - t0
     res = ws.warm_vs_cold(Lattice, net, test_mask, Q, TAU, c_kc, ref["k"], stream=stream,
-                          sync=torch.cuda.synchronize, max_steps=args.ws_ref_steps)
+                          sync=torch.cuda.synchronize, max_steps=args.ws_ref_steps, variant=args.variant)
     out = {"warmstart": {
         "train": {"samples": S, "side": side, "lbm_steps": args.ws_lbm_steps, "epochs": args.ws_epochs,
                   "loss_first": float(hist[0]), "loss_last": float(hist[-1]), "val_loss": val_loss,
                   "c_kc": c_kc, "seconds": {"geometry": round(t_geo, 1), "lbm": round(t_lbm, 1),
                                             "train": round(t_train, 1)}},
-        "test": {"side": args.ws_test, "k_ref": ref["k"], "k_ref_steps": ref["steps"],
+        "test": {"side": args.ws_test, "n_pore": n_test, "step_variant": args.variant,
+                 "k_ref": ref["k"], "k_ref_steps": ref["steps"], "k_ref_seconds": round(t_ref, 1),
                  "k_ref_converged": ref["converged"], **res}}}
     print(json.dumps(out), flush=True)
     net.close()
