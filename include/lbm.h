@@ -222,6 +222,41 @@ int lbm_batch_get_info(const lbm_batch* b, int64_t* n_pore, int64_t* n_tiles, in
 /* Profiling aid: n >= 1 single-step launches with CUDA events around each on the
  * batch's stream; mean device milliseconds per step.  Advances the state. */
 int lbm_batch_time_step(lbm_batch* b, int n, float* ms);
+
+/* Launch configurations of lbm_batch_step.  All compute the same steps; they differ
+ * in launch form and register cap.
+ *   LBM_BATCH_GRAPH (default): one launch per step, with one 256-node tile per block.
+ *     Runs of 64 steps replay a captured CUDA graph.
+ *   LBM_BATCH_PERSISTENT: one cooperative launch carries all steps of a call.  The
+ *     call is split at the 16-bit reference refreshes.  Blocks walk the tiles with
+ *     a grid stride, and a grid barrier separates the steps.  That barrier's wait
+ *     is bounded (2^31 SM cycles, about 1 s).  If a wait runs out, the call returns
+ *     LBM_ETIMEOUT and the state it leaves is incomplete.  The call synchronises
+ *     the stream to read that status.
+ *   *_CAPPED: the same launch compiled for 5 resident 256-thread blocks per SM
+ *     (48 registers) instead of 4 (64 registers).  There is no cap for FP64.
+ * lbm_batch_set_config selects a configuration.  lbm_batch_autotune measures
+ * them for you.  For every configuration it runs trial_steps steps untimed, then
+ * trial_steps timed steps, restoring the state after each run.  The restore uses
+ * a temporary device copy of the state (LBM_ENOMEM if there is no room).  It then
+ * selects the fastest: *best receives it, and ms_per_step[LBM_BATCH_NCONFIG] (may
+ * be NULL) the per-step times.  On return, the state, step count and boundary
+ * values are those before the call.  Both calls synchronise. */
+enum {
+    LBM_BATCH_GRAPH = 0,
+    LBM_BATCH_GRAPH_CAPPED = 1,
+    LBM_BATCH_PERSISTENT = 2,
+    LBM_BATCH_PERSISTENT_CAPPED = 3,
+    LBM_BATCH_NCONFIG = 4
+};
+int lbm_batch_set_config(lbm_batch* b, int config);
+int lbm_batch_autotune(lbm_batch* b, int trial_steps, int* best, float* ms_per_step);
+/* Diagnostic of the persistent launch's grid barrier (no effect on the state).
+ * Four blocks meet at a barrier expecting four arrivals (*completes = 1 if it
+ * completed), then at one expecting five, whose bounded wait must run out after
+ * about timeout_ms (0 < timeout_ms <= 2000) and be reported (*times_out = 1).
+ * The context stays usable either way.  Synchronises. */
+int lbm_batch_check_barrier(lbm_batch* b, double timeout_ms, int* completes, int* times_out);
 int lbm_batch_destroy(lbm_batch* b);
 const char* lbm_batch_last_error(const lbm_batch* b);
 

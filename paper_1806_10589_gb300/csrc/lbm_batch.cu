@@ -9,7 +9,11 @@
 // closures with the inlet density of Eq. potential, collision, store) with the
 // member's own boundary scalars; the next step's inlet density of every member
 // is formed in the same launch (FP64, deterministic last-tile finish per
-// member).  Runs of 64 steps replay a captured CUDA graph.
+// member).  Two launch forms: one launch per step, runs of 64 steps replaying a
+// captured CUDA graph; or one persistent cooperative launch for all steps of a
+// call, with a bounded grid barrier between steps.  Each form comes with two
+// register caps; lbm_batch_autotune times the four on the ensemble and keeps
+// the fastest.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -95,16 +99,33 @@ __device__ __forceinline__ typename S::M member_slope(const Member& m) {
     else return M(0);
 }
 
-template <class S, int Q>
-__device__ __forceinline__ typename S::M pull_b(const typename S::T* __restrict__ fin, int64_t ns,
+// Loads of values that other blocks of the same launch may have written (the
+// persistent launch: distributions and member scalars of the previous step) go
+// through L2 (ld.global.cg); per-step launches use ordinary loads.
+template <bool COH, class T>
+__device__ __forceinline__ T ld_state(const T* p) {
+    if constexpr (!COH) {
+        return *p;
+    } else if constexpr (sizeof(T) == 2) {
+        const unsigned short u = __ldcg(reinterpret_cast<const unsigned short*>(p));
+        T v;
+        memcpy(&v, &u, 2);
+        return v;
+    } else {
+        return __ldcg(p);
+    }
+}
+
+template <class S, int Q, bool COH = false>
+__device__ __forceinline__ typename S::M pull_b(const typename S::T* fin, int64_t ns,
                                                 const int* __restrict__ grid, const Member& m,
                                                 int64_t p, int64_t i, typename S::M r_own,
                                                 typename S::M g) {
     using M = typename S::M;
-    if (Q == 0) return S::template dec<0>(fin[i], r_own);
+    if (Q == 0) return S::template dec<0>(ld_state<COH>(fin + i), r_own);
     const int id = __ldg(grid + p + m.goff[Q]);
-    if (id >= 0) return S::template dec<Q>(fin[(int64_t)Q * ns + id], r_own - M(cz(Q)) * g);
-    return S::template dec<Q>(fin[(int64_t)opp(Q) * ns + i], r_own);
+    if (id >= 0) return S::template dec<Q>(ld_state<COH>(fin + (int64_t)Q * ns + id), r_own - M(cz(Q)) * g);
+    return S::template dec<Q>(ld_state<COH>(fin + (int64_t)opp(Q) * ns + i), r_own);
 }
 
 // Same contribution rule as the single-lattice step (see lbm_kernels.cu).
@@ -157,15 +178,15 @@ __device__ __forceinline__ void member_reduce(double part, int64_t tile, int64_t
     }
 }
 
-template <class S>
-__global__ void __launch_bounds__(kTile)
-k_batch_step(const typename S::T* __restrict__ fin, typename S::T* __restrict__ fout, int64_t ns, int slot,
-             const uint32_t* __restrict__ vox, const int* __restrict__ grid, const int* __restrict__ tile_member,
-             Member* members, typename S::M sp, typename S::M sm, double* __restrict__ partials,
-             unsigned* __restrict__ counters) {
+// One 256-node tile of one step: the single-lattice step with the member's own
+// boundary scalars, and the member's next inlet density (last tile finishes).
+template <class S, bool COH>
+__device__ __forceinline__ void batch_tile_step(const typename S::T* fin, typename S::T* fout, int64_t ns, int slot,
+                                                int64_t tile, const uint32_t* __restrict__ vox,
+                                                const int* __restrict__ grid, const int* __restrict__ tile_member,
+                                                Member* members, typename S::M sp, typename S::M sm,
+                                                double* partials, unsigned* counters, double* sh) {
     using M = typename S::M;
-    __shared__ double sh[32];
-    const int64_t tile = blockIdx.x;
     const int mi = tile_member[tile];
     const Member& m = members[mi];
     const int64_t tile0 = m.base / kTile;
@@ -175,14 +196,14 @@ k_batch_step(const typename S::T* __restrict__ fin, typename S::T* __restrict__ 
     if (il < m.n) {
         const int64_t p = vox[i];
         const M r_own = member_ref<S>(m, p), g = member_slope<S>(m);
-        const uint32_t seed = S::kRef ? m.sr_seed[slot] : 0u;
+        const uint32_t seed = S::kRef ? ld_state<COH>(&m.sr_seed[slot]) : 0u;
         M d[19];
         for_q(AllQ{}, [&](auto qc) {
             constexpr int Q = decltype(qc)::value;
-            d[Q] = pull_b<S, Q>(fin, ns, grid, m, p, i, r_own, g);
+            d[Q] = pull_b<S, Q, COH>(fin, ns, grid, m, p, i, r_own, g);
         });
         if (il < m.a_in) {
-            close_inlet(d, M(m.drho_in[slot]) - inlet_known(d));
+            close_inlet(d, M(ld_state<COH>(&m.drho_in[slot])) - inlet_known(d));
         } else if (il >= m.n - m.a_out) {
             close_outlet(d, outlet_known(d) - M(m.drho_out));
         }
@@ -197,8 +218,102 @@ k_batch_step(const typename S::T* __restrict__ fin, typename S::T* __restrict__ 
     if (tile - tile0 < nt01)
         member_reduce(part, tile, tile0, nt01, partials, counters + mi, sh, [&](double s) {
             members[mi].drho_in[slot ^ 1] = (m.Q + s) / (double)m.a_in;
-            if constexpr (S::kRef) members[mi].sr_seed[slot ^ 1] = sr_next(m.sr_seed[slot]);
+            if constexpr (S::kRef) members[mi].sr_seed[slot ^ 1] = sr_next(ld_state<COH>(&m.sr_seed[slot]));
         });
+}
+
+// Resident blocks per SM a configuration compiles for (register cap); FP64 is
+// left unconstrained.
+template <class S, int MINB>
+constexpr int batch_min_blocks() {
+    return sizeof(typename S::M) == 8 ? 1 : MINB;
+}
+
+// One step, one tile per block.
+template <class S, int MINB>
+__global__ void __launch_bounds__(kTile, batch_min_blocks<S, MINB>())
+k_batch_step(const typename S::T* __restrict__ fin, typename S::T* __restrict__ fout, int64_t ns, int slot,
+             const uint32_t* __restrict__ vox, const int* __restrict__ grid, const int* __restrict__ tile_member,
+             Member* members, typename S::M sp, typename S::M sm, double* __restrict__ partials,
+             unsigned* __restrict__ counters) {
+    __shared__ double sh[32];
+    batch_tile_step<S, false>(fin, fout, ns, slot, blockIdx.x, vox, grid, tile_member, members, sp, sm, partials,
+                              counters, sh);
+}
+
+// Grid barrier of the persistent launch.  Thread 0 of every block arrives on a
+// counter; the last arrival resets it and advances the generation, the others
+// wait for the generation to change.  The wait is bounded: after `limit` SM
+// cycles the block records a timeout and the caller returns, so a block that
+// never arrives cannot hang the GPU.
+struct GridBarrier {
+    unsigned count;
+    unsigned gen;
+    int err;
+    int pad;
+};
+
+__device__ __forceinline__ bool grid_barrier(GridBarrier* bar, unsigned nblocks, unsigned& gen, long long limit) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned g = gen;
+        __threadfence();
+        if (atomicAdd(&bar->count, 1u) == nblocks - 1) {
+            atomicExch(&bar->count, 0u);
+            __threadfence();
+            atomicExch(&bar->gen, g + 1u);
+            ok = 1;
+        } else {
+            ok = 0;
+            const long long t0 = clock64();
+            while (true) {
+                if (*(volatile unsigned*)&bar->gen != g) {
+                    ok = 1;
+                    break;
+                }
+                if (clock64() - t0 > limit) break;
+                __nanosleep(64);
+            }
+            if (!ok) atomicExch(&bar->err, 1);
+        }
+        __threadfence();
+        gen = g + 1u;
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// `nsteps` steps in one cooperative launch: blocks walk the tiles with a grid
+// stride, a bounded grid barrier separates the steps.  Step s reads buffer
+// slot0 ^ (s & 1).
+template <class S, int MINB>
+__global__ void __launch_bounds__(kTile, batch_min_blocks<S, MINB>())
+k_batch_persistent(typename S::T* f0, typename S::T* f1, int64_t ns, int slot0, int nsteps, int64_t ntiles,
+                   const uint32_t* __restrict__ vox, const int* __restrict__ grid,
+                   const int* __restrict__ tile_member, Member* members, typename S::M sp, typename S::M sm,
+                   double* partials, unsigned* counters, GridBarrier* bar, long long limit) {
+    __shared__ double sh[32];
+    unsigned gen = 0;
+    if (threadIdx.x == 0) gen = *(volatile unsigned*)&bar->gen;
+    for (int s = 0; s < nsteps; ++s) {
+        const int slot = slot0 ^ (s & 1);
+        const typename S::T* fin = slot ? f1 : f0;
+        typename S::T* fout = slot ? f0 : f1;
+        for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x)
+            batch_tile_step<S, true>(fin, fout, ns, slot, tile, vox, grid, tile_member, members, sp, sm, partials,
+                                     counters, sh);
+        if (!grid_barrier(bar, gridDim.x, gen, limit)) return;
+    }
+}
+
+// Barrier check: `nblocks` blocks meet at a barrier that expects `expected`
+// arrivals.  With expected == nblocks it completes; with more it must time out
+// and set the error flag.
+__global__ void k_barrier_probe(GridBarrier* bar, unsigned expected, long long limit) {
+    unsigned gen = 0;
+    if (threadIdx.x == 0) gen = *(volatile unsigned*)&bar->gen;
+    grid_barrier(bar, expected, gen, limit);
 }
 
 // Inlet density of every member by a pull over its inlet plane (states set
@@ -390,6 +505,8 @@ struct lbm_batch {
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     int64_t steps = 0, since_reencode = 0;
     int ref_e = 0;
+    int config = LBM_BATCH_GRAPH;      // launch form and register cap (lbm_batch_set_config)
+    lbm::GridBarrier* d_bar = nullptr;  // grid barrier of the persistent launch
     int status = LBM_OK;
     std::string err;
 };
@@ -438,7 +555,69 @@ void brelease(lbm_batch* b) {
     cudaFree(b->d_counters);
     cudaFree(b->d_counter1);
     cudaFree(b->d_out);
+    cudaFree(b->d_bar);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+}
+
+// Register cap of a configuration: 4 or 5 resident 256-thread blocks per SM
+// (64 or 48 registers).
+constexpr bool cfg_capped(int cfg) { return cfg == LBM_BATCH_GRAPH_CAPPED || cfg == LBM_BATCH_PERSISTENT_CAPPED; }
+constexpr bool cfg_persistent(int cfg) { return cfg >= LBM_BATCH_PERSISTENT; }
+// Bounded wait of the persistent barrier: 2^31 SM cycles (about 1 s at 2 GHz).
+constexpr long long kBarrierLimit = 1LL << 31;
+
+template <class S, int MINB>
+cudaError_t persistent_grid(int* grid, int64_t ntiles) {
+    int per_sm = 0, dev = 0, sms = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lbm::k_batch_persistent<S, MINB>,
+                                                                  lbm::kTile, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    *grid = (int)std::min<int64_t>((int64_t)per_sm * sms, ntiles);
+    return cudaSuccess;
+}
+
+// `nsteps` steps in one cooperative launch (the persistent configurations).
+int bpersistent(lbm_batch* b, int nsteps) {
+    BATCH_CUDA(b, cudaMemsetAsync(b->d_bar, 0, sizeof(lbm::GridBarrier), b->stream));
+    cudaError_t e = lbm::dispatch(b->prec, [&](auto s) {
+        using S = decltype(s);
+        using T = typename S::T;
+        using M = typename S::M;
+        auto launch = [&](auto minb) -> cudaError_t {
+            constexpr int MINB = decltype(minb)::value;
+            int grid = 0;
+            cudaError_t e2 = persistent_grid<S, MINB>(&grid, b->ntiles);
+            if (e2 != cudaSuccess) return e2;
+            T* f0 = (T*)b->f[0];
+            T* f1 = (T*)b->f[1];
+            int64_t ns = b->ns, ntiles = b->ntiles;
+            int slot0 = b->cur, n = nsteps;
+            M sp = (M)b->sp, sm = (M)b->sm;
+            long long limit = kBarrierLimit;
+            void* args[] = {&f0, &f1, &ns, &slot0, &n, &ntiles, &b->d_vox, &b->d_grid, &b->d_tile_member,
+                            &b->d_members, &sp, &sm, &b->d_partials, &b->d_counters, &b->d_bar, &limit};
+            return cudaLaunchCooperativeKernel((const void*)lbm::k_batch_persistent<S, MINB>, dim3(grid),
+                                               dim3(lbm::kTile), args, 0, b->stream);
+        };
+        if (cfg_capped(b->config)) return launch(std::integral_constant<int, 5>{});
+        return launch(std::integral_constant<int, 4>{});
+    });
+    BATCH_CUDA(b, e);
+    if (nsteps & 1) b->cur ^= 1;
+    return LBM_OK;
+}
+
+// The persistent launch records a barrier timeout in device memory.
+int bcheck_barrier(lbm_batch* b) {
+    lbm::GridBarrier h{};
+    BATCH_CUDA(b, cudaMemcpyAsync(&h, b->d_bar, sizeof h, cudaMemcpyDeviceToHost, b->stream));
+    BATCH_CUDA(b, cudaStreamSynchronize(b->stream));
+    if (h.err) return bfail(b, LBM_ETIMEOUT, "persistent launch: a block waited more than 2^31 cycles at the "
+                                             "step barrier; the state of this call is incomplete");
+    return LBM_OK;
 }
 
 int bstep_once(lbm_batch* b, cudaStream_t st) {
@@ -446,9 +625,14 @@ int bstep_once(lbm_batch* b, cudaStream_t st) {
         using S = decltype(s);
         using T = typename S::T;
         using M = typename S::M;
-        lbm::k_batch_step<S><<<(unsigned)b->ntiles, lbm::kTile, 0, st>>>(
-            (const T*)b->f[b->cur], (T*)b->f[b->cur ^ 1], b->ns, b->cur, b->d_vox, b->d_grid,
-            b->d_tile_member, b->d_members, (M)b->sp, (M)b->sm, b->d_partials, b->d_counters);
+        if (cfg_capped(b->config))
+            lbm::k_batch_step<S, 5><<<(unsigned)b->ntiles, lbm::kTile, 0, st>>>(
+                (const T*)b->f[b->cur], (T*)b->f[b->cur ^ 1], b->ns, b->cur, b->d_vox, b->d_grid,
+                b->d_tile_member, b->d_members, (M)b->sp, (M)b->sm, b->d_partials, b->d_counters);
+        else
+            lbm::k_batch_step<S, 4><<<(unsigned)b->ntiles, lbm::kTile, 0, st>>>(
+                (const T*)b->f[b->cur], (T*)b->f[b->cur ^ 1], b->ns, b->cur, b->d_vox, b->d_grid,
+                b->d_tile_member, b->d_members, (M)b->sp, (M)b->sm, b->d_partials, b->d_counters);
         return cudaGetLastError();
     });
     BATCH_CUDA(b, e);
@@ -635,6 +819,7 @@ int lbm_batch_create(int n_members, const uint8_t* const* masks, const int* dims
     A(&b->d_counters, (size_t)n_members * sizeof(unsigned));
     A(&b->d_counter1, sizeof(unsigned));
     A(&b->d_out, sizeof(double));
+    A(&b->d_bar, sizeof(lbm::GridBarrier));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMemcpy(b->d_vox, vox.data(), vox.size() * 4, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->d_grid, grid.data(), grid.size() * 4, cudaMemcpyHostToDevice);
@@ -645,6 +830,7 @@ int lbm_batch_create(int n_members, const uint8_t* const* masks, const int* dims
                        cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(b->d_counters, 0, (size_t)n_members * sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMemset(b->d_counter1, 0, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(b->d_bar, 0, sizeof(lbm::GridBarrier));
     // rest state: d = f - w = 0 in every format (the reference profile starts at 0)
     if (e == cudaSuccess) e = cudaMemset(b->f[0], 0, fbytes);
     if (e == cudaSuccess) e = cudaMemset(b->f[1], 0, fbytes);
@@ -691,6 +877,21 @@ int lbm_batch_step(lbm_batch* b, int n) {
     int rc = benter(b);
     if (rc) return rc;
     if (n < 0) return bfail(b, LBM_EINVAL, "n must be >= 0");
+    if (cfg_persistent(b->config)) {
+        // one cooperative launch per segment between 16-bit reference refreshes
+        int64_t k = 0;
+        while (k < n) {
+            if ((rc = bmaybe_reencode(b))) return rc;
+            int64_t seg = n - k;
+            if (b->prec >= LBM_PREC_FP16DEV) seg = std::min<int64_t>(seg, lbm::kBatchReencodeInterval - b->since_reencode);
+            if ((rc = bpersistent(b, (int)seg))) return rc;
+            k += seg;
+            b->since_reencode += seg;
+        }
+        if (n > 0 && (rc = bcheck_barrier(b))) return rc;
+        b->steps += n;
+        return LBM_OK;
+    }
     int k = 0;
     while (n - k >= lbm::kBatchGraphSteps) {
         if ((rc = bmaybe_reencode(b))) return rc;
@@ -716,7 +917,17 @@ int lbm_batch_time_step(lbm_batch* b, int n, float* ms) {
     BATCH_CUDA(b, cudaEventCreate(&e0));
     BATCH_CUDA(b, cudaEventCreate(&e1));
     double tot = 0.0;
-    for (int k = 0; k < n; ++k) {
+    if (cfg_persistent(b->config)) {
+        BATCH_CUDA(b, cudaEventRecord(e0, b->stream));
+        if ((rc = bpersistent(b, n))) return rc;
+        BATCH_CUDA(b, cudaEventRecord(e1, b->stream));
+        BATCH_CUDA(b, cudaEventSynchronize(e1));
+        float t = 0.f;
+        BATCH_CUDA(b, cudaEventElapsedTime(&t, e0, e1));
+        tot = t;
+        if ((rc = bcheck_barrier(b))) return rc;
+    }
+    for (int k = 0; k < n && !cfg_persistent(b->config); ++k) {
         BATCH_CUDA(b, cudaEventRecord(e0, b->stream));
         if ((rc = bstep_once(b, b->stream))) return rc;
         BATCH_CUDA(b, cudaEventRecord(e1, b->stream));
@@ -853,6 +1064,104 @@ int lbm_batch_get_info(const lbm_batch* b, int64_t* n_pore, int64_t* n_tiles, in
     if (n_pore) *n_pore = n;
     if (n_tiles) *n_tiles = b->ntiles;
     if (steps) *steps = b->steps;
+    return LBM_OK;
+}
+
+int lbm_batch_set_config(lbm_batch* b, int config) {
+    int rc = benter(b);
+    if (rc) return rc;
+    if (config < 0 || config >= LBM_BATCH_NCONFIG) return bfail(b, LBM_EINVAL, "unknown configuration %d", config);
+    BATCH_CUDA(b, cudaStreamSynchronize(b->stream));
+    for (auto& g : b->graph)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+    b->config = config;
+    return LBM_OK;
+}
+
+int lbm_batch_autotune(lbm_batch* b, int trial_steps, int* best, float* ms_per_step) {
+    int rc = benter(b);
+    if (rc) return rc;
+    if (trial_steps < 1) return bfail(b, LBM_EINVAL, "trial_steps must be >= 1");
+    const size_t fbytes = (size_t)19 * (size_t)b->ns * (size_t)(b->prec == 0 ? 8 : b->prec == 1 ? 4 : 2);
+    void* backup = nullptr;
+    if (cudaMalloc(&backup, fbytes) != cudaSuccess) {
+        cudaGetLastError();
+        return bfail(b, LBM_ENOMEM, "lbm_batch_autotune: no room for a copy of the state (%zu bytes)", fbytes);
+    }
+    // the trials start from, and leave behind, the state of this call
+    const int cur0 = b->cur, ref_e0 = b->ref_e, cfg0 = b->config;
+    const int64_t steps0 = b->steps, since0 = b->since_reencode;
+    auto save_restore = [&](bool save) -> int {
+        if (save) {
+            BATCH_CUDA(b, cudaStreamSynchronize(b->stream));
+            BATCH_CUDA(b, cudaMemcpy(backup, b->f[cur0], fbytes, cudaMemcpyDeviceToDevice));
+            BATCH_CUDA(b, cudaMemcpy(b->h_members.data(), b->d_members, (size_t)b->nm * sizeof(lbm::Member),
+                                     cudaMemcpyDeviceToHost));
+        } else {
+            BATCH_CUDA(b, cudaStreamSynchronize(b->stream));
+            BATCH_CUDA(b, cudaMemcpy(b->f[cur0], backup, fbytes, cudaMemcpyDeviceToDevice));
+            BATCH_CUDA(b, cudaMemcpy(b->d_members, b->h_members.data(), (size_t)b->nm * sizeof(lbm::Member),
+                                     cudaMemcpyHostToDevice));
+            b->cur = cur0;
+            b->ref_e = ref_e0;
+            b->steps = steps0;
+            b->since_reencode = since0;
+        }
+        return LBM_OK;
+    };
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    float t[LBM_BATCH_NCONFIG];
+    int choice = cfg0;
+    rc = save_restore(true);
+    if (rc == LBM_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+        rc = bfail(b, LBM_ECUDA, "lbm_batch_autotune: event creation failed");
+    for (int c = 0; c < LBM_BATCH_NCONFIG && rc == LBM_OK; ++c) {
+        if ((rc = lbm_batch_set_config(b, c))) break;
+        // untimed run first: graph capture and first-launch costs
+        if ((rc = lbm_batch_step(b, trial_steps)) || (rc = save_restore(false))) break;
+        if (cudaEventRecord(e0, b->stream) != cudaSuccess) { rc = bfail(b, LBM_ECUDA, "event record"); break; }
+        if ((rc = lbm_batch_step(b, trial_steps))) break;
+        if (cudaEventRecord(e1, b->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&t[c], e0, e1) != cudaSuccess) {
+            rc = bfail(b, LBM_ECUDA, "event timing");
+            break;
+        }
+        t[c] /= (float)trial_steps;
+        if ((rc = save_restore(false))) break;
+        if (t[c] < t[choice] || c == 0) choice = c;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(backup);
+    if (rc != LBM_OK) return rc;
+    if ((rc = lbm_batch_set_config(b, choice))) return rc;
+    if (best) *best = choice;
+    if (ms_per_step)
+        for (int c = 0; c < LBM_BATCH_NCONFIG; ++c) ms_per_step[c] = t[c];
+    return LBM_OK;
+}
+
+int lbm_batch_check_barrier(lbm_batch* b, double timeout_ms, int* completes, int* times_out) {
+    int rc = benter(b);
+    if (rc) return rc;
+    if (!(timeout_ms > 0.0) || timeout_ms > 2000.0) return bfail(b, LBM_EINVAL, "timeout_ms must be in (0, 2000]");
+    const long long limit = (long long)(timeout_ms * 2.1e6);  // cycles at up to 2.1 GHz
+    int got[2] = {0, 0};
+    for (int k = 0; k < 2; ++k) {
+        lbm::GridBarrier h{};
+        BATCH_CUDA(b, cudaMemsetAsync(b->d_bar, 0, sizeof h, b->stream));
+        lbm::k_barrier_probe<<<4, 32, 0, b->stream>>>(b->d_bar, k == 0 ? 4u : 5u, limit);
+        BATCH_CUDA(b, cudaGetLastError());
+        BATCH_CUDA(b, cudaMemcpyAsync(&h, b->d_bar, sizeof h, cudaMemcpyDeviceToHost, b->stream));
+        BATCH_CUDA(b, cudaStreamSynchronize(b->stream));
+        got[k] = h.err;
+    }
+    BATCH_CUDA(b, cudaMemsetAsync(b->d_bar, 0, sizeof(lbm::GridBarrier), b->stream));
+    if (completes) *completes = got[0] == 0;
+    if (times_out) *times_out = got[1] != 0;
     return LBM_OK;
 }
 

@@ -19,6 +19,9 @@ LIB_PATH = os.environ.get("GB300_LBM_LIB") or os.path.join(_HERE, "libgb300lbm.s
 LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSUPPORTED, LBM_EUNSTABLE, LBM_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
 LBM_MODEL_BGK, LBM_MODEL_MRT = 0, 1
 LBM_PREC_FP64, LBM_PREC_FP32, LBM_PREC_FP16DEV, LBM_PREC_BF16DEV = 0, 1, 2, 3
+LBM_BATCH_GRAPH, LBM_BATCH_GRAPH_CAPPED, LBM_BATCH_PERSISTENT, LBM_BATCH_PERSISTENT_CAPPED = 0, 1, 2, 3
+LBM_BATCH_NCONFIG = 4
+BATCH_CONFIGS = ("graph", "graph-capped", "persistent", "persistent-capped")
 LBM_FACE_ZMIN, LBM_FACE_ZMAX = 4, 5
 PRECISIONS = {"fp64": LBM_PREC_FP64, "fp32": LBM_PREC_FP32, "fp16dev": LBM_PREC_FP16DEV,
               "bf16dev": LBM_PREC_BF16DEV}
@@ -64,6 +67,9 @@ SIGNATURES = {
     "lbm_batch_get_fields": (C.c_int, [_P, C.c_int, _DP, _DP, _DP, _DP]),
     "lbm_batch_get_info": (C.c_int, [_P, _I64P, _I64P, _I64P]),
     "lbm_batch_time_step": (C.c_int, [_P, C.c_int, _FP]),
+    "lbm_batch_set_config": (C.c_int, [_P, C.c_int]),
+    "lbm_batch_autotune": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int), _FP]),
+    "lbm_batch_check_barrier": (C.c_int, [_P, C.c_double, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "lbm_batch_destroy": (C.c_int, [_P]),
     "lbm_batch_last_error": (C.c_char_p, [_P]),
     "lbm_color_create": (C.c_int, [C.POINTER(C.c_uint8), C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
@@ -349,6 +355,25 @@ class Batch:
         ms = C.c_float()
         self._check(self._lib.lbm_batch_time_step(self._h, int(n), C.byref(ms)))
         return ms.value
+
+    def set_config(self, config):
+        """Launch configuration (LBM_BATCH_*): per-step launches under a graph or
+        one persistent launch per call, each with a 64- or 48-register cap."""
+        self._check(self._lib.lbm_batch_set_config(self._h, int(config)))
+
+    def autotune(self, trial_steps=200):
+        """Time every configuration on this ensemble and keep the fastest; the
+        state is left as it was.  Returns (best, ms per step of each)."""
+        best = C.c_int()
+        ms = (C.c_float * LBM_BATCH_NCONFIG)()
+        self._check(self._lib.lbm_batch_autotune(self._h, int(trial_steps), C.byref(best), ms))
+        return best.value, [float(v) for v in ms]
+
+    def check_barrier(self, timeout_ms=20.0):
+        """(completes, times_out) of the persistent launch's grid barrier."""
+        a, b = C.c_int(), C.c_int()
+        self._check(self._lib.lbm_batch_check_barrier(self._h, float(timeout_ms), C.byref(a), C.byref(b)))
+        return bool(a.value), bool(b.value)
 
 
 class WarmStartNet:

@@ -84,3 +84,106 @@ def test_batch_rejects_bad_members(torch_cuda):
     bad[0] = 1
     with pytest.raises(LBMError):
         Batch([duct_mask(6, 6, 8), bad], 1.0)
+
+
+def _run_cfg(masks, prec, config, steps, torch, Qs=(0.001, 0.004, 0.02, 0.03)):
+    from paper_1806_10589_gb300 import Batch
+
+    with Batch(masks, 0.8, "mrt", prec, stream=torch.cuda.current_stream()) as b:
+        b.set_config(config)
+        for k, m in enumerate(masks):
+            b.set_flux_bc(k, Qs[k])
+            b.set_distributions(k, _f0(m, 10 + k))
+        b.step(steps)
+        return [b.distributions(k) for k in range(len(masks))], [b.get_flux(k, 4) for k in range(len(masks))]
+
+
+@pytest.mark.parametrize("config", [1, 2, 3])
+def test_batch_configs_fp64_match_oracle(torch_cuda, config):
+    """Every launch configuration (per-step launches with the 48-register cap,
+    one persistent launch with either cap) against the oracle, 70 steps: the
+    persistent launch carries all of them, with a grid barrier between steps."""
+    masks = _members()
+    Qs = [0.001, 0.004, 0.02, 0.03]
+    got, flux = _run_cfg(masks, "fp64", config, 70, torch_cuda)
+    for k, m in enumerate(masks):
+        ref = O.D3Q19Oracle(m, 0.8, "mrt", Q=Qs[k])
+        ref.set_distributions(_f0(m, 10 + k))
+        ref.step(70)
+        assert np.abs(got[k] - ref.f).max() / np.abs(ref.f).max() <= 1e-11, k
+        assert abs(flux[k][1] - ref.rho_in) <= 1e-12, k
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16dev"])
+def test_batch_configs_agree(torch_cuda, prec):
+    """The four configurations run the same per-node code: their states agree
+    (to an ulp of the largest deviation at most; bit equality is expected)."""
+    masks = _members()
+    ref, _ = _run_cfg(masks, prec, 0, 70, torch_cuda)
+    for config in (1, 2, 3):
+        got, _ = _run_cfg(masks, prec, config, 70, torch_cuda)
+        for k, m in enumerate(masks):
+            dev = np.abs(ref[k] - O.W[:, None, None, None] * (m == 0)).max()
+            tol = (4 * np.finfo(np.float32).eps if prec == "fp32" else 2.0 ** -9) * dev
+            assert np.abs(got[k] - ref[k]).max() <= tol, (config, k)
+
+
+def test_batch_autotune_keeps_state_and_picks_a_config(torch_cuda):
+    from paper_1806_10589_gb300 import Batch
+
+    masks = _members()
+    with Batch(masks, 0.8, "mrt", "fp32", stream=torch_cuda.cuda.current_stream()) as b:
+        for k, m in enumerate(masks):
+            b.set_flux_bc(k, 0.01)
+            b.set_distributions(k, _f0(m, 10 + k))
+        b.step(5)
+        before = [b.distributions(k) for k in range(len(masks))]
+        rho_before = [b.get_flux(k, 4)[1] for k in range(len(masks))]
+        steps_before = b.info()["steps"]
+        best, ms = b.autotune(70)
+        assert best in (0, 1, 2, 3) and len(ms) == 4 and all(t > 0 for t in ms)
+        assert ms[best] == min(ms)
+        for k in range(len(masks)):
+            np.testing.assert_array_equal(b.distributions(k), before[k])
+            assert b.get_flux(k, 4)[1] == rho_before[k]
+        assert b.info()["steps"] == steps_before
+        b.step(30)
+        after = [b.distributions(k) for k in range(len(masks))]
+    with Batch(masks, 0.8, "mrt", "fp32", stream=torch_cuda.cuda.current_stream()) as c:
+        for k, m in enumerate(masks):
+            c.set_flux_bc(k, 0.01)
+            c.set_distributions(k, _f0(m, 10 + k))
+        c.step(35)
+        for k, m in enumerate(masks):
+            dev = np.abs(after[k] - O.W[:, None, None, None] * (m == 0)).max()
+            assert np.abs(c.distributions(k) - after[k]).max() <= 4 * np.finfo(np.float32).eps * dev, k
+
+
+def test_batch_barrier_wait_is_bounded(torch_cuda):
+    """The persistent launch's grid barrier completes when every block arrives,
+    and reports (instead of hanging) when one never does; the ensemble keeps
+    working afterwards."""
+    from paper_1806_10589_gb300 import Batch
+
+    masks = _members()
+    with Batch(masks, 0.8, "mrt", "fp32", stream=torch_cuda.cuda.current_stream()) as b:
+        completes, times_out = b.check_barrier(20.0)
+        assert completes and times_out
+        b.set_config(2)
+        b.set_flux_bc(0, 0.001)
+        b.step(10)
+        assert np.isfinite(b.distributions(0)).all()
+
+
+@pytest.mark.parametrize("prec", ["fp16dev", "bf16dev"])
+def test_batch_persistent_crosses_reference_refresh(torch_cuda, prec):
+    """1100 steps in persistent launches split at the 16-bit reference refresh
+    (every 1024 steps) agree with the per-step launches to the storage rounding."""
+    masks = _members()[:3]
+    ref, fr = _run_cfg(masks, prec, 0, 1100, torch_cuda, Qs=(0.001, 0.004, 0.02))
+    got, fg = _run_cfg(masks, prec, 2, 1100, torch_cuda, Qs=(0.001, 0.004, 0.02))
+    bits = 11 if prec == "fp16dev" else 8
+    for k, m in enumerate(masks):
+        dev = np.abs(ref[k] - O.W[:, None, None, None] * (m == 0)).max()
+        assert np.abs(got[k] - ref[k]).max() <= 2.0 ** (2 - bits) * dev, k
+        assert abs(fg[k][1] - fr[k][1]) <= 0.05 * abs(fr[k][1] - 1), k
