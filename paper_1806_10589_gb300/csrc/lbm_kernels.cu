@@ -425,9 +425,14 @@ k_step(const StepPtrs<typename S::T> P, int slot, DevLattice L, typename S::M sp
 // Where the gather-scatter step keeps its 18 neighbour ids across the
 // collision (LBM_AA_IDS): 0 = registers (spills at the 64-register cap),
 // 1 = loads them again from the id grid, 2 = shared memory (18 KB per block).
+// Measured best: 1 for FP32 (and FP64), 2 for the 16-bit formats (LBM_AA16_IDS).
 #ifndef LBM_AA_IDS
 #define LBM_AA_IDS 1
 #endif
+#ifndef LBM_AA16_IDS
+#define LBM_AA16_IDS 2
+#endif
+
 
 // Row pointers of the single buffer as kernel parameters (constant bank), as
 // for k_step: no registers spent on 19 row addresses.
@@ -484,9 +489,8 @@ k_step_aa(const AAPtrs<typename S::T> F, int slot, DevLattice L, typename S::M s
     using M = typename S::M;
     __shared__ double sh[32];
     __shared__ bool last;
-#if LBM_AA_IDS == 2
-    __shared__ int sid[ODD ? 18 : 1][kBlock];
-#endif
+    constexpr int kIds = S::kRef ? LBM_AA16_IDS : LBM_AA_IDS;
+    __shared__ int sid[(ODD && kIds == 2) ? 18 : 1][kBlock];
     const int64_t i64 = (int64_t)blockIdx.x * kBlock + threadIdx.x;
     const int i = (int)i64;
     double part = 0.0;
@@ -508,9 +512,7 @@ k_step_aa(const AAPtrs<typename S::T> F, int slot, DevLattice L, typename S::M s
             for_q(std::make_integer_sequence<int, 18>{}, [&](auto qc) {
                 constexpr int Q = decltype(qc)::value + 1;
                 nb[Q] = ld_aa_index(L.grid + (uint32_t)(p + (uint32_t)L.goff[Q]), pol_idx);
-#if LBM_AA_IDS == 2
-                sid[Q - 1][threadIdx.x] = nb[Q];
-#endif
+                if constexpr (kIds == 2) sid[Q - 1][threadIdx.x] = nb[Q];
                 d[Q] = nb[Q] >= 0 ? S::template dec<Q>(F.row[opp(Q)][nb[Q]], r_own - M(cz(Q)) * g)
                                   : S::template dec<Q>(F.row[Q][i], r_own);
             });
@@ -533,22 +535,17 @@ k_step_aa(const AAPtrs<typename S::T> F, int slot, DevLattice L, typename S::M s
         int j;
         asm volatile("mov.b32 %0, %1;" : "=r"(j) : "r"(i));
         if constexpr (ODD) {
-#if LBM_AA_IDS == 1
-            // fresh policy and voxel index: nothing of the gather stays live
-            const uint64_t pol_s = aa_index_policy();
-            const uint32_t ps = ld_aa_index(L.vox + j, pol_s);
-#endif
+            // kIds == 1: fresh policy and voxel index, nothing of the gather stays live
+            const uint64_t pol_s = kIds == 1 ? aa_index_policy() : 0;
+            const uint32_t ps = kIds == 1 ? ld_aa_index(L.vox + j, pol_s) : 0u;
             F.row[0][j] = S::template enc_sr<0>(d[0], r_own, sr_key<S>(seed, i, 0));
             for_q(std::make_integer_sequence<int, 18>{}, [&](auto qc) {
                 constexpr int Q = decltype(qc)::value + 1;
                 // x + xi_Q is the pull source of opp(Q)
-#if LBM_AA_IDS == 1
-                const int dst = ld_aa_index(L.grid + (uint32_t)(ps + (uint32_t)L.goff[opp(Q)]), pol_s);
-#elif LBM_AA_IDS == 2
-                const int dst = sid[opp(Q) - 1][threadIdx.x];
-#else
-                const int dst = nb[opp(Q)];
-#endif
+                int dst;
+                if constexpr (kIds == 1) dst = ld_aa_index(L.grid + (uint32_t)(ps + (uint32_t)L.goff[opp(Q)]), pol_s);
+                else if constexpr (kIds == 2) dst = sid[opp(Q) - 1][threadIdx.x];
+                else dst = nb[opp(Q)];
                 const uint32_t key = sr_key<S>(seed, i, Q);
                 if (dst >= 0) F.row[Q][dst] = S::template enc_sr<Q>(d[Q], r_own + M(cz(Q)) * g, key);
                 else F.row[opp(Q)][j] = S::template enc_sr<Q>(d[Q], r_own, key);
