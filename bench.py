@@ -313,7 +313,7 @@ def run_ensemble(stream, prec="fp16dev", steps=2000, warmup=64):
             "ms_per_step": round(ms / steps, 5),
             "roofline": {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(ach / peak, 4),
-                         "kernel": "k_batch_persistent" if best >= 2 else "k_batch_step",
+                         "kernel": {2: "k_batch_persistent", 3: "k_batch_persistent", 4: "k_batch_aa", 5: "k_batch_aa"}.get(best, "k_batch_step"),
                          "kernel_ms": round(k_ms, 5), "bytes_per_unit": 2 * 19 * s},
             "autotune": {"chosen": BATCH_CONFIGS[best],
                          "ms_per_step": {BATCH_CONFIGS[c]: round(t, 5) for c, t in enumerate(trial_ms)}},

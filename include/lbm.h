@@ -233,6 +233,10 @@ int lbm_batch_time_step(lbm_batch* b, int n, float* ms);
  *     is bounded (2^31 SM cycles, about 1 s).  If a wait runs out, the call returns
  *     LBM_ETIMEOUT and the state it leaves is incomplete.  The call synchronises
  *     the stream to read that status.
+ *   LBM_BATCH_AA: the AA pattern of lbm_set_kernel variant 3 on the shared store.
+ *     Steps alternate a gather-scatter and a node-local launch under a captured
+ *     graph, with in-place layout swaps around each call.  Both buffers stay
+ *     allocated.
  *   *_CAPPED: the same launch compiled for 5 resident 256-thread blocks per SM
  *     (48 registers) instead of 4 (64 registers).  There is no cap for FP64.
  * lbm_batch_set_config selects a configuration.  lbm_batch_autotune measures
@@ -247,7 +251,9 @@ enum {
     LBM_BATCH_GRAPH_CAPPED = 1,
     LBM_BATCH_PERSISTENT = 2,
     LBM_BATCH_PERSISTENT_CAPPED = 3,
-    LBM_BATCH_NCONFIG = 4
+    LBM_BATCH_AA = 4,
+    LBM_BATCH_AA_CAPPED = 5,
+    LBM_BATCH_NCONFIG = 6
 };
 int lbm_batch_set_config(lbm_batch* b, int config);
 int lbm_batch_autotune(lbm_batch* b, int trial_steps, int* best, float* ms_per_step);

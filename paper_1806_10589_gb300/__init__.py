@@ -8,5 +8,5 @@ from .lbm import (  # noqa: F401
     Lattice, Batch, ColorLattice, WarmStartNet, LBMError, load_library, LIB_PATH, SIGNATURES,
     LBM_FACE_ZMIN, LBM_FACE_ZMAX, LBM_PREC_FP64, LBM_PREC_FP32, LBM_PREC_FP16DEV, LBM_PREC_BF16DEV,
     LBM_MODEL_BGK, LBM_MODEL_MRT, PRECISIONS, MODELS, BATCH_CONFIGS, LBM_BATCH_GRAPH, LBM_BATCH_GRAPH_CAPPED,
-    LBM_BATCH_PERSISTENT, LBM_BATCH_PERSISTENT_CAPPED,
+    LBM_BATCH_PERSISTENT, LBM_BATCH_PERSISTENT_CAPPED, LBM_BATCH_AA, LBM_BATCH_AA_CAPPED,
 )

@@ -316,6 +316,166 @@ __global__ void k_barrier_probe(GridBarrier* bar, unsigned expected, long long l
     grid_barrier(bar, expected, gen, limit);
 }
 
+// ----------------------------------------------------- AA pattern (batch) ---
+// The single-lattice AA pattern (see lbm_kernels.cu) on the shared store: the
+// state rests in the pull layout between calls; a call swaps every node's
+// opposite pairs, alternates gather-scatter (odd) and node-local (even) steps,
+// and swaps back (after an odd count an un-stream swap comes first).  Ids are
+// global pore indices, so the scatter stays inside the member.  16-bit values
+// are encoded with the reference of the plane of the node that holds them; the
+// gather-scatter step loads its ids again for the scatter.
+// Row pointers of the store as kernel parameters (constant bank): no registers
+// spent on 19 row addresses.
+template <class T>
+struct Rows {
+    T* row[19];
+};
+
+template <class S, bool ODD, int MINB>
+__global__ void __launch_bounds__(kTile, batch_min_blocks<S, MINB>())
+k_batch_aa(const Rows<typename S::T> F, int slot, const uint32_t* __restrict__ vox,
+           const int* __restrict__ grid, const int* __restrict__ tile_member, Member* members, typename S::M sp,
+           typename S::M sm, double* __restrict__ partials, unsigned* __restrict__ counters) {
+    using M = typename S::M;
+    __shared__ double sh[32];
+    const int64_t tile = blockIdx.x;
+    const int mi = tile_member[tile];
+    const Member& m = members[mi];
+    const int64_t tile0 = m.base / kTile;
+    const int64_t i = tile * kTile + threadIdx.x;
+    const int64_t il = i - m.base;
+    double part = 0.0;
+    if (il < m.n) {
+        const int64_t p = vox[i];
+        const M r_own = member_ref<S>(m, p), g = member_slope<S>(m);
+        const uint32_t seed = S::kRef ? m.sr_seed[slot] : 0u;
+        M d[19];
+        if constexpr (ODD) {
+            d[0] = S::template dec<0>(F.row[0][i], r_own);
+            for_q(std::make_integer_sequence<int, 18>{}, [&](auto qc) {
+                constexpr int Q = decltype(qc)::value + 1;
+                const int id = __ldg(grid + p + m.goff[Q]);
+                d[Q] = id >= 0 ? S::template dec<Q>(F.row[opp(Q)][id], r_own - M(cz(Q)) * g)
+                               : S::template dec<Q>(F.row[Q][i], r_own);
+            });
+        } else {
+            for_q(AllQ{}, [&](auto qc) {
+                constexpr int Q = decltype(qc)::value;
+                d[Q] = S::template dec<Q>(F.row[Q][i], r_own);
+            });
+        }
+        if (il < m.a_in) {
+            close_inlet(d, M(m.drho_in[slot]) - inlet_known(d));
+        } else if (il >= m.n - m.a_out) {
+            close_outlet(d, outlet_known(d) - M(m.drho_out));
+        }
+        collide(d, sp, sm);
+        // an opaque copy of the node index for the stores (sharing the load
+        // addresses would keep 19 64-bit addresses live across the collision)
+        int64_t j;
+        asm volatile("mov.b64 %0, %1;" : "=l"(j) : "l"(i));
+        if constexpr (ODD) {
+            const int64_t ps = __ldg(vox + j);
+            F.row[0][j] = S::template enc_sr<0>(d[0], r_own, sr_key<S>(seed, i, 0));
+            for_q(std::make_integer_sequence<int, 18>{}, [&](auto qc) {
+                constexpr int Q = decltype(qc)::value + 1;
+                const int dst = __ldg(grid + ps + m.goff[opp(Q)]);  // x + xi_Q is the pull source of opp(Q)
+                const uint32_t key = sr_key<S>(seed, i, Q);
+                if (dst >= 0) F.row[Q][dst] = S::template enc_sr<Q>(d[Q], r_own + M(cz(Q)) * g, key);
+                else F.row[opp(Q)][j] = S::template enc_sr<Q>(d[Q], r_own, key);
+            });
+        } else {
+            for_q(AllQ{}, [&](auto qc) {
+                constexpr int Q = decltype(qc)::value;
+                F.row[opp(Q)][j] = S::template enc_sr<Q>(d[Q], r_own, sr_key<S>(seed, i, Q));
+            });
+        }
+        if (il < m.a_01) {
+            // the counted values land on plane 0 (odd step: from plane 1 encoded with plane 0's reference)
+            auto val = [&](auto qc) -> double {
+                constexpr int Q = decltype(qc)::value;
+                const M rq = (ODD && cz(Q) < 0) ? r_own - g : r_own;
+                return (double)S::template dec<Q>(S::template enc_sr<Q>(d[Q], rq, sr_key<S>(seed, i, Q)), rq);
+            };
+            auto dest_is_pore = [&](auto qc) -> bool {
+                constexpr int Q = decltype(qc)::value;
+                return __ldg(grid + p + m.goff[opp(Q)]) >= 0;
+            };
+            if (il < m.a_in) {
+                for_q(std::integer_sequence<int, 0, 1, 2, 3, 4, 7, 8, 9, 10>{}, [&](auto qc) { part += val(qc); });
+                for_q(std::integer_sequence<int, 5, 11, 14, 15, 18>{},
+                      [&](auto qc) { if (!dest_is_pore(qc)) part += 2.0 * val(qc); });
+            } else {
+                for_q(std::integer_sequence<int, 6, 12, 13, 16, 17>{},
+                      [&](auto qc) { if (dest_is_pore(qc)) part += 2.0 * val(qc); });
+            }
+        }
+    }
+    const int64_t nt01 = (m.a_01 + kTile - 1) / kTile;
+    if (tile - tile0 < nt01)
+        member_reduce(part, tile, tile0, nt01, partials, counters + mi, sh, [&](double s) {
+            members[mi].drho_in[slot ^ 1] = (m.Q + s) / (double)m.a_in;
+            if constexpr (S::kRef) members[mi].sr_seed[slot ^ 1] = sr_next(m.sr_seed[slot]);
+        });
+}
+
+// Opposite-pair swap of every slot (padding slots included; they are never read).
+template <class T>
+__global__ void k_batch_aa_swap(T* __restrict__ f, int64_t total, int64_t ns) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= total) return;
+    T v[19];
+#pragma unroll
+    for (int q = 1; q < 19; ++q) v[q] = f[(int64_t)q * ns + i];
+#pragma unroll
+    for (int q = 1; q < 19; q += 2) {
+        f[(int64_t)q * ns + i] = v[q + 1];
+        f[(int64_t)(q + 1) * ns + i] = v[q];
+    }
+}
+
+// Layout I -> S after an odd step count (pairwise swap with the pull source,
+// 16-bit values re-encoded to their new holder's plane).
+template <class S>
+__global__ void __launch_bounds__(kTile)
+k_batch_aa_unstream(typename S::T* __restrict__ f, int64_t ns, const uint32_t* __restrict__ vox,
+                    const int* __restrict__ grid, const int* __restrict__ tile_member, const Member* members) {
+    using M = typename S::M;
+    using T = typename S::T;
+    const int64_t tile = blockIdx.x;
+    const Member& m = members[tile_member[tile]];
+    const int64_t i = tile * kTile + threadIdx.x;
+    if (i - m.base >= m.n) return;
+    const int64_t p = vox[i];
+    const M r_own = member_ref<S>(m, p), g = member_slope<S>(m);
+    int id[19];
+    T ta[19], tb[19];
+    for_q(std::integer_sequence<int, 1, 3, 5, 7, 9, 11, 13, 15, 17>{}, [&](auto qc) {
+        constexpr int Q = decltype(qc)::value;
+        id[Q] = __ldg(grid + p + m.goff[Q]);
+    });
+    for_q(std::integer_sequence<int, 1, 3, 5, 7, 9, 11, 13, 15, 17>{}, [&](auto qc) {
+        constexpr int Q = decltype(qc)::value;
+        if (id[Q] >= 0) {
+            ta[Q] = f[(int64_t)Q * ns + i];
+            tb[Q] = f[(int64_t)(Q + 1) * ns + id[Q]];
+        }
+    });
+    for_q(std::integer_sequence<int, 1, 3, 5, 7, 9, 11, 13, 15, 17>{}, [&](auto qc) {
+        constexpr int Q = decltype(qc)::value;
+        if (id[Q] >= 0) {
+            if constexpr (S::kRef) {
+                const M r_src = r_own - M(cz(Q)) * g;
+                f[(int64_t)Q * ns + i] = S::template enc<Q>(S::template dec<Q>(tb[Q], r_src), r_own);
+                f[(int64_t)(Q + 1) * ns + id[Q]] = S::template enc<Q>(S::template dec<Q>(ta[Q], r_own), r_src);
+            } else {
+                f[(int64_t)Q * ns + i] = tb[Q];
+                f[(int64_t)(Q + 1) * ns + id[Q]] = ta[Q];
+            }
+        }
+    });
+}
+
 // Inlet density of every member by a pull over its inlet plane (states set
 // from outside a step).  Grid: all tiles; tiles past a member's inlet exit.
 template <class S>
@@ -561,8 +721,14 @@ void brelease(lbm_batch* b) {
 
 // Register cap of a configuration: 4 or 5 resident 256-thread blocks per SM
 // (64 or 48 registers).
-constexpr bool cfg_capped(int cfg) { return cfg == LBM_BATCH_GRAPH_CAPPED || cfg == LBM_BATCH_PERSISTENT_CAPPED; }
-constexpr bool cfg_persistent(int cfg) { return cfg >= LBM_BATCH_PERSISTENT; }
+constexpr bool cfg_capped(int cfg) {
+    return cfg == LBM_BATCH_GRAPH_CAPPED || cfg == LBM_BATCH_PERSISTENT_CAPPED || cfg == LBM_BATCH_AA_CAPPED;
+}
+constexpr bool cfg_persistent(int cfg) { return cfg == LBM_BATCH_PERSISTENT || cfg == LBM_BATCH_PERSISTENT_CAPPED; }
+constexpr bool cfg_aa(int cfg) { return cfg == LBM_BATCH_AA || cfg == LBM_BATCH_AA_CAPPED; }
+// Buffer that holds the state: f[cur] for the pull forms, f[0] for the AA
+// pattern (cur is then only the parity of the inlet-density slot).
+void* bstate(lbm_batch* b) { return cfg_aa(b->config) ? b->f[0] : b->f[b->cur]; }
 // Bounded wait of the persistent barrier: 2^31 SM cycles (about 1 s at 2 GHz).
 constexpr long long kBarrierLimit = 1LL << 31;
 
@@ -640,12 +806,55 @@ int bstep_once(lbm_batch* b, cudaStream_t st) {
     return LBM_OK;
 }
 
+// One AA step of a call: gather-scatter when odd is set, node-local otherwise.
+int bstep_aa(lbm_batch* b, cudaStream_t st, bool odd) {
+    cudaError_t e = lbm::dispatch(b->prec, [&](auto s) {
+        using S = decltype(s);
+        using T = typename S::T;
+        using M = typename S::M;
+        auto go = [&](auto oddc, auto minbc) {
+            constexpr bool ODD = decltype(oddc)::value;
+            constexpr int MINB = decltype(minbc)::value;
+            lbm::Rows<T> F;
+            for (int q = 0; q < 19; ++q) F.row[q] = (T*)b->f[0] + (int64_t)q * b->ns;
+            lbm::k_batch_aa<S, ODD, MINB><<<(unsigned)b->ntiles, lbm::kTile, 0, st>>>(
+                F, b->cur, b->d_vox, b->d_grid, b->d_tile_member, b->d_members, (M)b->sp, (M)b->sm,
+                b->d_partials, b->d_counters);
+        };
+        const bool capped = cfg_capped(b->config);
+        if (odd && capped) go(std::true_type{}, std::integral_constant<int, 5>{});
+        else if (odd) go(std::true_type{}, std::integral_constant<int, 4>{});
+        else if (capped) go(std::false_type{}, std::integral_constant<int, 5>{});
+        else go(std::false_type{}, std::integral_constant<int, 4>{});
+        return cudaGetLastError();
+    });
+    BATCH_CUDA(b, e);
+    b->cur ^= 1;
+    return LBM_OK;
+}
+
+int baa_layout(lbm_batch* b, bool unstream) {
+    cudaError_t e = lbm::dispatch(b->prec, [&](auto s) {
+        using S = decltype(s);
+        using T = typename S::T;
+        if (unstream)
+            lbm::k_batch_aa_unstream<S><<<(unsigned)b->ntiles, lbm::kTile, 0, b->stream>>>(
+                (T*)b->f[0], b->ns, b->d_vox, b->d_grid, b->d_tile_member, b->d_members);
+        else
+            lbm::k_batch_aa_swap<T><<<(unsigned)((b->total + 255) / 256), 256, 0, b->stream>>>((T*)b->f[0], b->total,
+                                                                                             b->ns);
+        return cudaGetLastError();
+    });
+    BATCH_CUDA(b, e);
+    return LBM_OK;
+}
+
 int bprime(lbm_batch* b) {
     cudaError_t e = lbm::dispatch(b->prec, [&](auto s) {
         using S = decltype(s);
         using T = typename S::T;
         lbm::k_batch_inlet<S><<<(unsigned)b->ntiles, lbm::kTile, 0, b->stream>>>(
-            (const T*)b->f[b->cur], b->ns, b->cur, b->d_vox, b->d_grid, b->d_tile_member, b->d_members,
+            (const T*)bstate(b), b->ns, b->cur, b->d_vox, b->d_grid, b->d_tile_member, b->d_members,
             b->d_partials, b->d_counters);
         return cudaGetLastError();
     });
@@ -660,7 +869,7 @@ int bmaybe_reencode(lbm_batch* b) {
         using T = typename S::T;
         if constexpr (S::kRef) {
             lbm::k_batch_reencode<S><<<(unsigned)b->ntiles, lbm::kTile, 0, b->stream>>>(
-                (T*)b->f[b->cur], b->ns, b->d_vox, b->d_tile_member, b->d_members, b->ref_e, b->cur, b->total);
+                (T*)bstate(b), b->ns, b->d_vox, b->d_tile_member, b->d_members, b->ref_e, b->cur, b->total);
         }
         return cudaGetLastError();
     });
@@ -676,7 +885,8 @@ int bbuild_graph(lbm_batch* b, int parity) {
     cudaGraph_t g = nullptr;
     BATCH_CUDA(b, cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
     int rc = LBM_OK;
-    for (int k = 0; k < lbm::kBatchGraphSteps && rc == LBM_OK; ++k) rc = bstep_once(b, b->cap_stream);
+    for (int k = 0; k < lbm::kBatchGraphSteps && rc == LBM_OK; ++k)
+        rc = cfg_aa(b->config) ? bstep_aa(b, b->cap_stream, (k & 1) == 0) : bstep_once(b, b->cap_stream);
     cudaError_t e = cudaStreamEndCapture(b->cap_stream, &g);
     b->cur = saved;
     if (rc != LBM_OK) {
@@ -877,6 +1087,30 @@ int lbm_batch_step(lbm_batch* b, int n) {
     int rc = benter(b);
     if (rc) return rc;
     if (n < 0) return bfail(b, LBM_EINVAL, "n must be >= 0");
+    if (cfg_aa(b->config)) {
+        // segments end at the 16-bit reference refreshes, which work on the pull layout
+        int64_t k = 0;
+        while (k < n) {
+            if ((rc = bmaybe_reencode(b))) return rc;
+            int64_t seg = n - k;
+            if (b->prec >= LBM_PREC_FP16DEV) seg = std::min<int64_t>(seg, lbm::kBatchReencodeInterval - b->since_reencode);
+            if ((rc = baa_layout(b, false))) return rc;
+            int64_t j = 0;
+            while (seg - j >= lbm::kBatchGraphSteps) {
+                if (!b->graph[b->cur] && (rc = bbuild_graph(b, b->cur))) return rc;
+                BATCH_CUDA(b, cudaGraphLaunch(b->graph[b->cur], b->stream));
+                j += lbm::kBatchGraphSteps;
+            }
+            for (; j < seg; ++j)
+                if ((rc = bstep_aa(b, b->stream, (j & 1) == 0))) return rc;
+            if ((seg & 1) && (rc = baa_layout(b, true))) return rc;
+            if ((rc = baa_layout(b, false))) return rc;
+            k += seg;
+            b->since_reencode += seg;
+        }
+        b->steps += n;
+        return LBM_OK;
+    }
     if (cfg_persistent(b->config)) {
         // one cooperative launch per segment between 16-bit reference refreshes
         int64_t k = 0;
@@ -927,7 +1161,19 @@ int lbm_batch_time_step(lbm_batch* b, int n, float* ms) {
         tot = t;
         if ((rc = bcheck_barrier(b))) return rc;
     }
-    for (int k = 0; k < n && !cfg_persistent(b->config); ++k) {
+    if (cfg_aa(b->config)) {
+        // the AA steps of one call (the layout swaps included)
+        BATCH_CUDA(b, cudaEventRecord(e0, b->stream));
+        if ((rc = lbm_batch_step(b, n))) return rc;
+        BATCH_CUDA(b, cudaEventRecord(e1, b->stream));
+        BATCH_CUDA(b, cudaEventSynchronize(e1));
+        float t = 0.f;
+        BATCH_CUDA(b, cudaEventElapsedTime(&t, e0, e1));
+        tot = t;
+        b->steps -= n;  // counted below
+        b->since_reencode -= n;
+    }
+    for (int k = 0; k < n && !cfg_persistent(b->config) && !cfg_aa(b->config); ++k) {
         BATCH_CUDA(b, cudaEventRecord(e0, b->stream));
         if ((rc = bstep_once(b, b->stream))) return rc;
         BATCH_CUDA(b, cudaEventRecord(e1, b->stream));
@@ -955,7 +1201,7 @@ int lbm_batch_get_flux(lbm_batch* b, int member, int face, double* Q, double* rh
     cudaError_t e = lbm::dispatch(b->prec, [&](auto s) {
         using S = decltype(s);
         lbm::k_batch_face_flux<S><<<nt, lbm::kTile, 0, b->stream>>>(
-            (const typename S::T*)b->f[b->cur], b->ns, b->d_vox, b->d_members, member,
+            (const typename S::T*)bstate(b), b->ns, b->d_vox, b->d_members, member,
             face == LBM_FACE_ZMIN ? 0 : 1, b->d_partials, b->d_counter1, b->d_out);
         return cudaGetLastError();
     });
@@ -980,7 +1226,7 @@ int lbm_batch_get_distributions(lbm_batch* b, int member, double* f) {
     cudaError_t e = lbm::dispatch(b->prec, [&](auto s) {
         using S = decltype(s);
         lbm::k_batch_decode<S><<<(unsigned)((m.n + lbm::kTile - 1) / lbm::kTile), lbm::kTile, 0, b->stream>>>(
-            (const typename S::T*)b->f[b->cur], b->ns, b->d_vox, b->d_members, member, d);
+            (const typename S::T*)bstate(b), b->ns, b->d_vox, b->d_members, member, d);
         return cudaGetLastError();
     });
     if (e == cudaSuccess)
@@ -1015,7 +1261,7 @@ int lbm_batch_set_distributions(lbm_batch* b, int member, const double* f) {
         e = lbm::dispatch(b->prec, [&](auto s) {
             using S = decltype(s);
             lbm::k_batch_encode<S><<<(unsigned)((m.n + lbm::kTile - 1) / lbm::kTile), lbm::kTile, 0, b->stream>>>(
-                (typename S::T*)b->f[b->cur], b->ns, b->d_vox, b->d_members, member, d);
+                (typename S::T*)bstate(b), b->ns, b->d_vox, b->d_members, member, d);
             return cudaGetLastError();
         });
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
@@ -1042,7 +1288,7 @@ int lbm_batch_get_fields(lbm_batch* b, int member, double* rho, double* ux, doub
         e = lbm::dispatch(b->prec, [&](auto s) {
             using S = decltype(s);
             lbm::k_batch_export<S><<<(unsigned)((m.n + lbm::kTile - 1) / lbm::kTile), lbm::kTile, 0, b->stream>>>(
-                (const typename S::T*)b->f[b->cur], b->ns, b->d_vox, b->d_members, member, dv, d, d + ncell,
+                (const typename S::T*)bstate(b), b->ns, b->d_vox, b->d_members, member, dv, d, d + ncell,
                 d + 2 * ncell, d + 3 * ncell);
             return cudaGetLastError();
         });
@@ -1077,6 +1323,8 @@ int lbm_batch_set_config(lbm_batch* b, int config) {
             cudaGraphExecDestroy(g);
             g = nullptr;
         }
+    // the AA pattern keeps the state in f[0]: move it between f[0] and f[cur]
+    if (cfg_aa(b->config) != cfg_aa(config) && b->cur == 1) std::swap(b->f[0], b->f[1]);
     b->config = config;
     return LBM_OK;
 }
@@ -1097,15 +1345,15 @@ int lbm_batch_autotune(lbm_batch* b, int trial_steps, int* best, float* ms_per_s
     auto save_restore = [&](bool save) -> int {
         if (save) {
             BATCH_CUDA(b, cudaStreamSynchronize(b->stream));
-            BATCH_CUDA(b, cudaMemcpy(backup, b->f[cur0], fbytes, cudaMemcpyDeviceToDevice));
+            BATCH_CUDA(b, cudaMemcpy(backup, bstate(b), fbytes, cudaMemcpyDeviceToDevice));
             BATCH_CUDA(b, cudaMemcpy(b->h_members.data(), b->d_members, (size_t)b->nm * sizeof(lbm::Member),
                                      cudaMemcpyDeviceToHost));
         } else {
             BATCH_CUDA(b, cudaStreamSynchronize(b->stream));
-            BATCH_CUDA(b, cudaMemcpy(b->f[cur0], backup, fbytes, cudaMemcpyDeviceToDevice));
+            b->cur = cur0;
+            BATCH_CUDA(b, cudaMemcpy(bstate(b), backup, fbytes, cudaMemcpyDeviceToDevice));
             BATCH_CUDA(b, cudaMemcpy(b->d_members, b->h_members.data(), (size_t)b->nm * sizeof(lbm::Member),
                                      cudaMemcpyHostToDevice));
-            b->cur = cur0;
             b->ref_e = ref_e0;
             b->steps = steps0;
             b->since_reencode = since0;

@@ -590,15 +590,19 @@ k_step_aa(const AAPtrs<typename S::T> F, int slot, DevLattice L, typename S::M s
 }
 
 // Pull layout <-> layout S: swap F[q][x] and F[opp q][x] at every node.
+// All 18 loads are issued before any store (the rows of one buffer could alias
+// as far as the compiler knows, which would serialise load-store pairs).
 template <class T>
 __global__ void k_aa_swap(T* __restrict__ f, int64_t n, int64_t ns) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    T v[19];
+#pragma unroll
+    for (int q = 1; q < 19; ++q) v[q] = f[(int64_t)q * ns + i];
 #pragma unroll
     for (int q = 1; q < 19; q += 2) {  // opposite pairs are (q, q + 1), q odd
-        const T a = f[(int64_t)q * ns + i];
-        f[(int64_t)q * ns + i] = f[(int64_t)(q + 1) * ns + i];
-        f[(int64_t)(q + 1) * ns + i] = a;
+        f[(int64_t)q * ns + i] = v[q + 1];
+        f[(int64_t)(q + 1) * ns + i] = v[q];
     }
 }
 
@@ -617,20 +621,32 @@ __global__ void k_aa_unstream(typename S::T* __restrict__ f, DevLattice L, const
     if (i >= L.n) return;
     const uint32_t p = L.vox[i];
     const M r_own = own_ref<S>(bc, L, p), g = own_slope<S>(bc);
+    // ids and values first, stores after (see k_aa_swap)
+    int id[19];
+    T ta[19], tb[19];
     for_q(std::integer_sequence<int, 1, 3, 5, 7, 9, 11, 13, 15, 17>{}, [&](auto qc) {
         constexpr int Q = decltype(qc)::value;
-        const int id = __ldg(L.grid + (uint32_t)(p + (uint32_t)L.goff[Q]));
-        if (id >= 0) {
+        id[Q] = __ldg(L.grid + (uint32_t)(p + (uint32_t)L.goff[Q]));
+    });
+    for_q(std::integer_sequence<int, 1, 3, 5, 7, 9, 11, 13, 15, 17>{}, [&](auto qc) {
+        constexpr int Q = decltype(qc)::value;
+        if (id[Q] >= 0) {
+            ta[Q] = f[(int64_t)Q * L.ns + i];
+            tb[Q] = f[(int64_t)(Q + 1) * L.ns + id[Q]];
+        }
+    });
+    for_q(std::integer_sequence<int, 1, 3, 5, 7, 9, 11, 13, 15, 17>{}, [&](auto qc) {
+        constexpr int Q = decltype(qc)::value;
+        if (id[Q] >= 0) {
             T* a = f + (int64_t)Q * L.ns + i;
-            T* b = f + (int64_t)(Q + 1) * L.ns + id;
-            const T ta = *a, tb = *b;
+            T* b = f + (int64_t)(Q + 1) * L.ns + id[Q];
             if constexpr (S::kRef) {
                 const M r_src = r_own - M(cz(Q)) * g;  // plane of x - xi_Q
-                *a = S::template enc<Q>(S::template dec<Q>(tb, r_src), r_own);
-                *b = S::template enc<Q>(S::template dec<Q>(ta, r_own), r_src);
+                *a = S::template enc<Q>(S::template dec<Q>(tb[Q], r_src), r_own);
+                *b = S::template enc<Q>(S::template dec<Q>(ta[Q], r_own), r_src);
             } else {
-                *a = tb;
-                *b = ta;
+                *a = tb[Q];
+                *b = ta[Q];
             }
         }
     });

@@ -20,8 +20,9 @@ LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSUPPORTED, LBM_EUNSTABLE, LBM_
 LBM_MODEL_BGK, LBM_MODEL_MRT = 0, 1
 LBM_PREC_FP64, LBM_PREC_FP32, LBM_PREC_FP16DEV, LBM_PREC_BF16DEV = 0, 1, 2, 3
 LBM_BATCH_GRAPH, LBM_BATCH_GRAPH_CAPPED, LBM_BATCH_PERSISTENT, LBM_BATCH_PERSISTENT_CAPPED = 0, 1, 2, 3
-LBM_BATCH_NCONFIG = 4
-BATCH_CONFIGS = ("graph", "graph-capped", "persistent", "persistent-capped")
+LBM_BATCH_AA, LBM_BATCH_AA_CAPPED = 4, 5
+LBM_BATCH_NCONFIG = 6
+BATCH_CONFIGS = ("graph", "graph-capped", "persistent", "persistent-capped", "aa", "aa-capped")
 LBM_FACE_ZMIN, LBM_FACE_ZMAX = 4, 5
 PRECISIONS = {"fp64": LBM_PREC_FP64, "fp32": LBM_PREC_FP32, "fp16dev": LBM_PREC_FP16DEV,
               "bf16dev": LBM_PREC_BF16DEV}
@@ -357,8 +358,9 @@ class Batch:
         return ms.value
 
     def set_config(self, config):
-        """Launch configuration (LBM_BATCH_*): per-step launches under a graph or
-        one persistent launch per call, each with a 64- or 48-register cap."""
+        """Launch configuration (LBM_BATCH_*): per-step launches under a graph,
+        one persistent launch per call, or the AA pattern, each with a 64- or
+        48-register cap."""
         self._check(self._lib.lbm_batch_set_config(self._h, int(config)))
 
     def autotune(self, trial_steps=200):

@@ -98,11 +98,13 @@ def _run_cfg(masks, prec, config, steps, torch, Qs=(0.001, 0.004, 0.02, 0.03)):
         return [b.distributions(k) for k in range(len(masks))], [b.get_flux(k, 4) for k in range(len(masks))]
 
 
-@pytest.mark.parametrize("config", [1, 2, 3])
+@pytest.mark.parametrize("config", [1, 2, 3, 4, 5])
 def test_batch_configs_fp64_match_oracle(torch_cuda, config):
     """Every launch configuration (per-step launches with the 48-register cap,
-    one persistent launch with either cap) against the oracle, 70 steps: the
-    persistent launch carries all of them, with a grid barrier between steps."""
+    one persistent launch with either cap, the AA pattern with either cap)
+    against the oracle, 70 steps: the persistent launch carries all of them,
+    with a grid barrier between steps; the AA pattern runs a 64-step graph and
+    six single steps."""
     masks = _members()
     Qs = [0.001, 0.004, 0.02, 0.03]
     got, flux = _run_cfg(masks, "fp64", config, 70, torch_cuda)
@@ -116,15 +118,22 @@ def test_batch_configs_fp64_match_oracle(torch_cuda, config):
 
 @pytest.mark.parametrize("prec", ["fp32", "fp16dev"])
 def test_batch_configs_agree(torch_cuda, prec):
-    """The four configurations run the same per-node code: their states agree
-    (to an ulp of the largest deviation at most; bit equality is expected)."""
+    """The configurations compute the same steps: the pull forms run the same
+    per-node code (agreement to an ulp of the largest deviation at most); the AA
+    pattern may contract products into FMAs differently and, in 16 bits,
+    encodes scattered values with another plane's reference, so it agrees to
+    rounding accumulated over the 70 steps (N eps max|d| in FP32, the storage
+    rounding in FP16)."""
     masks = _members()
     ref, _ = _run_cfg(masks, prec, 0, 70, torch_cuda)
-    for config in (1, 2, 3):
+    for config in (1, 2, 3, 4, 5):
         got, _ = _run_cfg(masks, prec, config, 70, torch_cuda)
         for k, m in enumerate(masks):
             dev = np.abs(ref[k] - O.W[:, None, None, None] * (m == 0)).max()
-            tol = (4 * np.finfo(np.float32).eps if prec == "fp32" else 2.0 ** -9) * dev
+            if config >= 4:
+                tol = (70 * np.finfo(np.float32).eps if prec == "fp32" else 8 * 70 * 2.0 ** -11) * dev
+            else:
+                tol = (4 * np.finfo(np.float32).eps if prec == "fp32" else 2.0 ** -9) * dev
             assert np.abs(got[k] - ref[k]).max() <= tol, (config, k)
 
 
@@ -141,7 +150,7 @@ def test_batch_autotune_keeps_state_and_picks_a_config(torch_cuda):
         rho_before = [b.get_flux(k, 4)[1] for k in range(len(masks))]
         steps_before = b.info()["steps"]
         best, ms = b.autotune(70)
-        assert best in (0, 1, 2, 3) and len(ms) == 4 and all(t > 0 for t in ms)
+        assert best in range(6) and len(ms) == 6 and all(t > 0 for t in ms)
         assert ms[best] == min(ms)
         for k in range(len(masks)):
             np.testing.assert_array_equal(b.distributions(k), before[k])
@@ -156,7 +165,8 @@ def test_batch_autotune_keeps_state_and_picks_a_config(torch_cuda):
         c.step(35)
         for k, m in enumerate(masks):
             dev = np.abs(after[k] - O.W[:, None, None, None] * (m == 0)).max()
-            assert np.abs(c.distributions(k) - after[k]).max() <= 4 * np.finfo(np.float32).eps * dev, k
+            # the chosen configuration may be the AA pattern: agreement to rounding over 35 steps
+            assert np.abs(c.distributions(k) - after[k]).max() <= 35 * np.finfo(np.float32).eps * dev, k
 
 
 def test_batch_barrier_wait_is_bounded(torch_cuda):
@@ -175,13 +185,15 @@ def test_batch_barrier_wait_is_bounded(torch_cuda):
         assert np.isfinite(b.distributions(0)).all()
 
 
+@pytest.mark.parametrize("config", [2, 4])
 @pytest.mark.parametrize("prec", ["fp16dev", "bf16dev"])
-def test_batch_persistent_crosses_reference_refresh(torch_cuda, prec):
-    """1100 steps in persistent launches split at the 16-bit reference refresh
-    (every 1024 steps) agree with the per-step launches to the storage rounding."""
+def test_batch_segments_cross_reference_refresh(torch_cuda, prec, config):
+    """1100 steps in persistent launches, or AA calls, split at the 16-bit
+    reference refresh (every 1024 steps) agree with the per-step launches to the
+    storage rounding."""
     masks = _members()[:3]
     ref, fr = _run_cfg(masks, prec, 0, 1100, torch_cuda, Qs=(0.001, 0.004, 0.02))
-    got, fg = _run_cfg(masks, prec, 2, 1100, torch_cuda, Qs=(0.001, 0.004, 0.02))
+    got, fg = _run_cfg(masks, prec, config, 1100, torch_cuda, Qs=(0.001, 0.004, 0.02))
     bits = 11 if prec == "fp16dev" else 8
     for k, m in enumerate(masks):
         dev = np.abs(ref[k] - O.W[:, None, None, None] * (m == 0)).max()
