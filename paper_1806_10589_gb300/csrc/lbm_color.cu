@@ -163,32 +163,50 @@ k_color_pre(const T* __restrict__ f, T* __restrict__ A, T* __restrict__ B, T* __
     }
 }
 
+// Row pointers of the two momentum buffers and the D3Q7 buffers of this step, as
+// kernel parameters (constant bank): no registers spent on row addresses.
 template <class T>
-__global__ void __launch_bounds__(kCB)
-k_color_step(const T* __restrict__ fin, T* __restrict__ fout, const T* __restrict__ Ain, T* __restrict__ Aout,
-             const T* __restrict__ Bin, T* __restrict__ Bout, const T* __restrict__ phi, DevLattice L,
-             const ColorParams* __restrict__ prm, T sp, T sm, T alpha, T beta, T phi_s) {
+struct ColorRows {
+    const T* fin[19];
+    T* fout[19];
+    const T* ain[7];
+    T* aout[7];
+    const T* bin[7];
+    T* bout[7];
+};
+
+#ifndef LBM_COLOR_MIN_BLOCKS
+#define LBM_COLOR_MIN_BLOCKS 4
+#endif
+template <class T>
+constexpr int color_min_blocks() {
+    return sizeof(T) == 8 ? 1 : LBM_COLOR_MIN_BLOCKS;
+}
+
+template <class T>
+__global__ void __launch_bounds__(kCB, color_min_blocks<T>())
+k_color_step(const ColorRows<T> R, const T* __restrict__ phi, DevLattice L, const ColorParams* __restrict__ prm,
+             T sp, T sm, T alpha, T beta, T phi_s) {
     const int64_t i64 = (int64_t)blockIdx.x * kCB + threadIdx.x;
     if (i64 >= L.n) return;
     const int i = (int)i64;
-    const int64_t p = L.vox[i];
+    const uint64_t pol = l2_policy_evict_last();  // index structures stay in L2
+    const uint32_t p = ld_hint(reinterpret_cast<const unsigned*>(L.vox) + i, pol);
     const T phi_own = phi[i];
     T d[19];
-    int idax[7];  // destination ids of the six D3Q7 axis directions (index q = 1..6)
     T cgx = 0, cgy = 0, cgz = 0;
-    d[0] = fin[i];
+    d[0] = R.fin[0][i];
     for_q(std::make_integer_sequence<int, 18>{}, [&](auto qc) {
         constexpr int Q = decltype(qc)::value + 1;
-        const int id = __ldg(L.grid + p + grid_off<Q>(L.sy, L.sz));
-        d[Q] = id >= 0 ? fin[(int64_t)Q * L.ns + id] : fin[(int64_t)opp(Q) * L.ns + i];
+        const int id = ld_hint(L.grid + (uint32_t)(p + (uint32_t)grid_off<Q>(L.sy, L.sz)), pol);
+        d[Q] = id >= 0 ? R.fin[Q][id] : R.fin[opp(Q)][i];
         // colour-gradient neighbour x + xi_opp(Q) is the pull source of Q
         const T ph = id >= 0 ? phi[id] : (id == SOLID ? phi_s : phi_own);  // box faces: own phi
-        constexpr int R = opp(Q);  // this neighbour sits at x + xi_R
-        const T wq3 = T(3.0 * wq(R));
-        if (cx(R)) cgx += wq3 * T(cx(R)) * ph;
-        if (cy(R)) cgy += wq3 * T(cy(R)) * ph;
-        if (cz(R)) cgz += wq3 * T(cz(R)) * ph;
-        if (R <= 6) idax[R] = id;  // push destination of D3Q7 direction R
+        constexpr int Rq = opp(Q);  // this neighbour sits at x + xi_Rq
+        const T wq3 = T(3.0 * wq(Rq));
+        if (cx(Rq)) cgx += wq3 * T(cx(Rq)) * ph;
+        if (cy(Rq)) cgy += wq3 * T(cy(Rq)) * ph;
+        if (cz(Rq)) cgz += wq3 * T(cz(Rq)) * ph;
     });
     if (i < L.a_in) {
         close_inlet(d, T(prm->drho_in) - inlet_known(d));
@@ -205,21 +223,26 @@ k_color_step(const T* __restrict__ fin, T* __restrict__ fout, const T* __restric
     const T dm1 = a, dm9 = T(0.5) * a * (T(2) * nx * nx - ny * ny - nz * nz), dm11 = T(0.5) * a * (ny * ny - nz * nz);
     const T dm13 = T(0.5) * a * nx * ny, dm14 = T(0.5) * a * ny * nz, dm15 = T(0.5) * a * nx * nz;
     collide(d, sp, sm);
+    // an opaque copy of i for the stores (sharing the load addresses would keep
+    // them live across the collision)
+    int j;
+    asm volatile("mov.b32 %0, %1;" : "=r"(j) : "r"(i));
     for_q(AllQ{}, [&](auto qc) {
         constexpr int Q = decltype(qc)::value;
         const T df = T(mrow(1, Q) / mnorm2(1)) * dm1 + T(mrow(9, Q) / mnorm2(9)) * dm9 +
                      T(mrow(11, Q) / mnorm2(11)) * dm11 + T(mrow(13, Q) / mnorm2(13)) * dm13 +
                      T(mrow(14, Q) / mnorm2(14)) * dm14 + T(mrow(15, Q) / mnorm2(15)) * dm15;
-        fout[(int64_t)Q * L.ns + i] = d[Q] + sp * df;
+        R.fout[Q][j] = d[Q] + sp * df;
     });
-    // D3Q7 mass transport with recolouring (push)
+    // D3Q7 mass transport with recolouring (push); destinations looked up again
     T na = 0, nb = 0;
 #pragma unroll
     for (int q = 0; q < 7; ++q) {
-        na += Ain[(int64_t)q * L.ns + i];
-        nb += Bin[(int64_t)q * L.ns + i];
+        na += R.ain[q][j];
+        nb += R.bin[q][j];
     }
-    const bool inlet = i < L.a_in, outlet = i64 >= L.n - L.a_out;
+    const bool inlet = j < L.a_in, outlet = (int64_t)j >= L.n - L.a_out;
+    const uint32_t ps = ld_hint(reinterpret_cast<const unsigned*>(L.vox) + j, pol);
     for_q(std::make_integer_sequence<int, 7>{}, [&](auto qc) {
         constexpr int Q = decltype(qc)::value;
         const T xu = T(cx(Q)) * jx + T(cy(Q)) * jy + T(cz(Q)) * jz;
@@ -227,26 +250,27 @@ k_color_step(const T* __restrict__ fin, T* __restrict__ fout, const T* __restric
         const T va = T(w7(Q)) * na * (T(1) + T(4.5) * xu + beta * nb * xn);
         const T vb = T(w7(Q)) * nb * (T(1) + T(4.5) * xu - beta * na * xn);
         if constexpr (Q == 0) {
-            Aout[i] = va;
-            Bout[i] = vb;
+            R.aout[0][j] = va;
+            R.bout[0][j] = vb;
         } else {
-            const int id = idax[Q];
+            // push destination x + xi_Q is the pull source of opp(Q)
+            const int id = ld_hint(L.grid + (uint32_t)(ps + (uint32_t)grid_off<opp(Q)>(L.sy, L.sz)), pol);
             if (id >= 0) {
-                Aout[(int64_t)Q * L.ns + id] = va;
-                Bout[(int64_t)Q * L.ns + id] = vb;
+                R.aout[Q][id] = va;
+                R.bout[Q][id] = vb;
             } else if (id != ZOUT) {  // solid voxel or lateral box face: bounce back
-                Aout[(int64_t)opp(Q) * L.ns + i] = va;
-                Bout[(int64_t)opp(Q) * L.ns + i] = vb;
+                R.aout[opp(Q)][j] = va;
+                R.bout[opp(Q)][j] = vb;
             }
         }
     });
     if (inlet) {  // the value entering through the inlet plane: set by the next pre-pass
-        Aout[(int64_t)5 * L.ns + i] = T(0);
-        Bout[(int64_t)5 * L.ns + i] = T(0);
+        R.aout[5][j] = T(0);
+        R.bout[5][j] = T(0);
     }
     if (outlet) {  // the value entering through the outlet plane (direction 6)
-        Aout[(int64_t)6 * L.ns + i] = T(w7(6)) * na * (T(1) - T(4.5) * jz);
-        Bout[(int64_t)6 * L.ns + i] = T(w7(6)) * nb * (T(1) - T(4.5) * jz);
+        R.aout[6][j] = T(w7(6)) * na * (T(1) - T(4.5) * jz);
+        R.bout[6][j] = T(w7(6)) * nb * (T(1) - T(4.5) * jz);
     }
 }
 
@@ -417,10 +441,19 @@ int cstep_once(lbm_color* c) {
         using T = decltype(zero);
         lbm::k_color_pre<T><<<nb, lbm::kCB, 0, c->stream>>>((const T*)c->f[k], (T*)c->A[k], (T*)c->B[k],
                                                            (T*)c->phi, c->L, c->d_prm, c->d_partials, c->d_counter);
-        lbm::k_color_step<T><<<nb, lbm::kCB, 0, c->stream>>>(
-            (const T*)c->f[k], (T*)c->f[k ^ 1], (const T*)c->A[k], (T*)c->A[k ^ 1], (const T*)c->B[k],
-            (T*)c->B[k ^ 1], (const T*)c->phi, c->L, c->d_prm, (T)c->sp, (T)c->sm, (T)c->alpha, (T)c->beta,
-            (T)c->phi_s);
+        lbm::ColorRows<T> R;
+        for (int q = 0; q < 19; ++q) {
+            R.fin[q] = (const T*)c->f[k] + (int64_t)q * c->L.ns;
+            R.fout[q] = (T*)c->f[k ^ 1] + (int64_t)q * c->L.ns;
+        }
+        for (int q = 0; q < 7; ++q) {
+            R.ain[q] = (const T*)c->A[k] + (int64_t)q * c->L.ns;
+            R.aout[q] = (T*)c->A[k ^ 1] + (int64_t)q * c->L.ns;
+            R.bin[q] = (const T*)c->B[k] + (int64_t)q * c->L.ns;
+            R.bout[q] = (T*)c->B[k ^ 1] + (int64_t)q * c->L.ns;
+        }
+        lbm::k_color_step<T><<<nb, lbm::kCB, 0, c->stream>>>(R, (const T*)c->phi, c->L, c->d_prm, (T)c->sp,
+                                                             (T)c->sm, (T)c->alpha, (T)c->beta, (T)c->phi_s);
         return cudaGetLastError();
     });
     COLOR_CUDA(c, e);
