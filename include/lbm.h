@@ -163,9 +163,12 @@ int lbm_get_info(const lbm_ctx* ctx, int64_t* n_pore, int64_t* a_in, int64_t* a_
                  int64_t* steps);
 
 /* Profiling aid: run n >= 1 steps as individual kernel launches on the context's
- * stream with CUDA events around each launch and return the mean device time
- * in milliseconds of the collide-stream kernel and of the inlet reduction
- * kernel (either pointer may be NULL).  Advances the state by n steps exactly
+ * stream, with CUDA events around each step launch.  Returns the mean device time
+ * in milliseconds of the step kernel.  On variant 3 that is the mean over the
+ * alternating gather-scatter and node-local launches; with n = 1 it is the
+ * gather-scatter launch alone.  The layout swaps around the launches are not
+ * timed.  The second output is 0, because the inlet reduction runs inside the
+ * step kernel.  Either pointer may be NULL.  Advances the state by n steps exactly
  * like lbm_step(ctx, n).  Synchronises. */
 int lbm_time_kernels(lbm_ctx* ctx, int n, float* ms_step_kernel, float* ms_inlet_kernel);
 
