@@ -279,7 +279,73 @@ def ensemble_workload(n_members=64, seed=7):
     return masks, Qs, edges
 
 
-def run_ensemble(stream, prec="fp16dev", steps=2000, warmup=64):
+def ensemble_steady(masks, Qs, stream, config, prec="fp16dev", max_steps=40000, every=200, hold=10, rtol=1e-3):
+    """Cold start of the ensemble in launch configuration `config`, run for
+    max_steps, recording every
+    member's permeability k(t) (Darcy, from the inlet density) and outlet flux
+    every `every` steps.  Each member's k_inf is its value at the end of the run
+    (its flatness over the last fifth is reported).  A member is steady from the
+    first check after which |k - k_inf| <= rtol k_inf and |Q_out - Q| <= rtol Q
+    hold for `hold` consecutive checks; the ensemble is steady when its last
+    member is."""
+    import torch
+
+    from paper_1806_10589_gb300 import Batch, convergence as cv
+
+    nm = len(masks)
+    ks, qs = [], []
+    with Batch(masks, TAU, "mrt", prec, stream=stream) as b:
+        b.set_config(config)
+        for m, q in enumerate(Qs):
+            b.set_flux_bc(m, q)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(max_steps // every):
+            b.step(every)
+            row_k, row_q = [], []
+            for m in range(nm):
+                q_out, _ = b.get_flux(m, 5)
+                _, rho_in = b.get_flux(m, 4)
+                row_k.append(cv.permeability(Qs[m], masks[m].shape, TAU, rho_in, 1.0))
+                row_q.append(q_out)
+            ks.append(row_k)
+            qs.append(row_q)
+        torch.cuda.synchronize()
+        secs = time.perf_counter() - t0
+    out = steady_summary(np.array(ks), np.array(qs), Qs, every, hold, rtol, max_steps)
+    out["seconds_run"] = round(secs, 2)
+    return out
+
+
+def steady_summary(ks, qs, Qs, every, hold, rtol, max_steps):
+    """Per-member time to the 0.1 % rule from recorded histories ks, qs
+    (checks x members): k_inf = the last k of each member."""
+    nm = ks.shape[1]
+    Qa = np.asarray(Qs, dtype=float)
+    k_inf = ks[-1]
+    tail = ks[int(0.8 * len(ks)):]
+    flat = float(np.max(np.abs(tail - k_inf) / k_inf))
+    ok = (np.abs(ks - k_inf) <= rtol * k_inf) & (np.abs(qs - Qa) <= rtol * Qa)
+    first = []
+    for m in range(nm):
+        run, start = 0, None
+        for t in range(len(ok)):
+            run = run + 1 if ok[t, m] else 0
+            if run == 1:
+                start = t
+            if run >= hold:
+                break
+        first.append((start + 1) * every if run >= hold else None)
+    reached = [f for f in first if f is not None]
+    crit = (f"k within {100 * rtol:g}% of the member's k at the end of a {max_steps}-step run and outlet flux "
+            f"within {100 * rtol:g}% of Q_i, for {hold} consecutive checks every {every} steps")
+    return {"criterion": crit, "members_reached": len(reached), "members": nm,
+            "steps_all_steady": max(reached) if len(reached) == nm else None,
+            "steps_median_member": int(np.median(reached)) if reached else None,
+            "k_inf_flatness_last_fifth": flat}
+
+
+def run_ensemble(stream, prec="fp16dev", steps=2000, warmup=64, steady_steps=True):
     """Throughput of the batched ensemble step in the launch configuration the
     library's autotuner picks (per-step launches under a graph or one persistent
     launch; two register caps each), and the step's HBM roofline."""
@@ -304,6 +370,7 @@ def run_ensemble(stream, prec="fp16dev", steps=2000, warmup=64):
         k_ms = b.time_step(100)
         n = b.info()["n_pore"]
         fl = [b.get_flux(k, 4)[0] for k in range(len(masks))]
+    steady = ensemble_steady(masks, Qs, stream, best, prec) if steady_steps else None
     s = BYTES_PER_VALUE[prec]
     peak, _ = measured_hbm_peak()
     ach = 2 * 19 * s * n / (k_ms * 1e-3) / 1e9
@@ -317,7 +384,8 @@ def run_ensemble(stream, prec="fp16dev", steps=2000, warmup=64):
                          "kernel_ms": round(k_ms, 5), "bytes_per_unit": 2 * 19 * s},
             "autotune": {"chosen": BATCH_CONFIGS[best],
                          "ms_per_step": {BATCH_CONFIGS[c]: round(t, 5) for c, t in enumerate(trial_ms)}},
-            "max_inlet_flux_rel_err": max(abs(f - q) / q for f, q in zip(fl, Qs))}
+            "max_inlet_flux_rel_err": max(abs(f - q) / q for f, q in zip(fl, Qs)),
+            "steady": steady}
 
 
 def laplace_gamma(stream, alpha=0.01, beta=0.95, n=48, R=12.0, steps=3000):

@@ -50,3 +50,25 @@ def test_single_rank_aggregate_is_local():
 
     v, ms = bench.aggregate(2000, 10, 4.0, 1)
     assert ms == 4.0 and abs(v - 2000 * 10 / 4e-3 / 1e6) < 1e-12
+
+
+def test_ensemble_steady_summary():
+    """Post-processing of the ensemble's steady-state run: a member is steady
+    from the first of `hold` consecutive checks within the tolerance."""
+    import numpy as np
+
+    import bench
+
+    every, hold = 100, 3
+    t = np.arange(1, 21)[:, None]
+    # member 0 relaxes like 1 + e^{-t/2}, member 1 never settles its outlet flux
+    ks = np.hstack([1.0 + np.exp(-t / 2.0), np.ones_like(t, dtype=float)])
+    qs = np.hstack([np.ones_like(t, dtype=float), 1.0 + 0.01 * (-1.0) ** t])
+    out = bench.steady_summary(ks, qs, [1.0, 1.0], every, hold, 1e-3, 2000)
+    # member 0 is steady from the first check within 1e-3 of its final k (all later ones are too)
+    k_inf = ks[-1, 0]
+    first_ok = int(np.argmax(np.abs(ks[:, 0] - k_inf) <= 1e-3 * k_inf))
+    assert out["members_reached"] == 1 and out["members"] == 2
+    assert out["steps_all_steady"] is None
+    assert out["steps_median_member"] == (first_ok + 1) * every
+    assert "0.1%" in out["criterion"]
