@@ -286,8 +286,8 @@ const char* lbm_last_error(const lbm_ctx* ctx);
  * contributes phi_s (wetting: +1 = the solid looks like phase A), a neighbour
  * outside the box (any face) the node's own phi, so the box faces are
  * wetting-neutral walls (they still bounce momentum and phases back); the inlet plane holds the injected composition
- * (N_A = rho_in (1 + phi_in)/2, N_B = rho_in (1 - phi_in)/2, set on the value that
- * entered through the inlet), the outlet lets both phases leave with their local
+ * (N_A = (1 + phi_in)/2, N_B = (1 - phi_in)/2 at the reference density 1, set on
+ * the value that entered through the inlet), the outlet lets both phases leave with their local
  * composition.  FP64 or FP32
  * storage.  A mask whose z = 0 (z = nz-1) plane is all solid has no inlet
  * (outlet) condition, so closed boxes are allowed.

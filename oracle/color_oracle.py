@@ -26,10 +26,11 @@ Readings where the paper is silent (also listed in the design notes):
     sender in the opposite direction; the inlet plane holds the injected
     composition: at the start of every step the D3Q7 value that entered an inlet
     node through the inlet (direction 5) is set so that the node carries
-    N_A = rho_in (1 + phi_in)/2 and N_B = rho_in (1 - phi_in)/2, rho_in the inlet
-    density of the previous step (phi_in = +1: the non-wetting phase A is
-    injected); at the outlet the entering value is w6 N [1 - 9/2 u_z] with the
-    node's own N_A, N_B, u_z;
+    N_A = rho0 (1 + phi_in)/2 and N_B = rho0 (1 - phi_in)/2 with rho0 = 1 (the
+    phase densities are transported at the reference density of the
+    incompressible model; the momentum density carries the pressure) (phi_in =
+    +1: the non-wetting phase A is injected); at the outlet the entering value is
+    w6 N [1 - 9/2 u_z] with the node's own N_A, N_B, u_z;
   * the collision uses the velocity and colour field of the same step; the
     mass transport uses u = j after the boundary closures.
 """
@@ -149,11 +150,11 @@ class ColourOracle:
 
     def hold_inlet_composition(self):
         """Set the D3Q7 value that entered each inlet node through the inlet
-        (direction 5) so the node carries N_A = rho_in (1 + phi_in)/2 and
-        N_B = rho_in (1 - phi_in)/2 (reading above)."""
+        (direction 5) so the node carries N_A = rho0 (1 + phi_in)/2 and
+        N_B = rho0 (1 - phi_in)/2, rho0 = 1 (reading above)."""
         frac = (1.0 + self.phi_in) / 2.0
         pore0 = self.pore[0]
-        for arr, target in ((self.A, self.rho_in * frac), (self.B, self.rho_in * (1.0 - frac))):
+        for arr, target in ((self.A, L.RHO0 * frac), (self.B, L.RHO0 * (1.0 - frac))):
             others = arr[:, 0].sum(axis=0) - arr[5, 0]
             arr[5, 0] = np.where(pore0, target - others, 0.0)
 

@@ -13,7 +13,8 @@
 //                 to x + xi_q, bouncing back from solids and lateral box faces; the outlet takes
 //                 w6 N (1 - 9/2 u_z).  The inlet plane holds the injected
 //                 composition: the pre-pass sets the value that entered each inlet
-//                 node through the inlet so the node carries rho_in (1 +- phi_in)/2.
+//                 node through the inlet so the node carries rho0 (1 +- phi_in)/2,
+//                 rho0 = 1.
 // Momentum distributions are stored shifted (d = f - w) as in the single-fluid
 // path; A and B are stored as they are.
 #include <cuda_runtime.h>
@@ -119,14 +120,13 @@ k_color_pre(const T* __restrict__ f, T* __restrict__ A, T* __restrict__ B, T* __
             nb += B[(int64_t)q * L.ns + i];
         }
         if (i64 < L.a_in) {
-            // injected composition: the density of the previous step (read before
-            // this launch's last block replaces it)
-            const T rin = T(1) + T(prm->drho_in);
+            // injected composition at the reference density rho0 = 1 (the momentum
+            // density carries the pressure, the phase densities do not)
             const T fa = (T(1) + T(prm->phi_in)) * T(0.5);
-            A[(int64_t)5 * L.ns + i] = rin * fa - na;
-            B[(int64_t)5 * L.ns + i] = rin * (T(1) - fa) - nb;
-            na = rin * fa;
-            nb = rin * (T(1) - fa);
+            A[(int64_t)5 * L.ns + i] = fa - na;
+            B[(int64_t)5 * L.ns + i] = (T(1) - fa) - nb;
+            na = fa;
+            nb = T(1) - fa;
         }
         phi[i] = (na - nb) / (na + nb);
         if (i64 < L.a_in) {
