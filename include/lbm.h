@@ -44,7 +44,9 @@ typedef enum {
  * 8(2 - s_nu)/(8 - s_nu); because every D3Q19 moment is even or odd in xi and
  * the rates split the same way, it is evaluated as the equivalent
  * two-relaxation-time update (s+ = s_nu, s- = s_q). */
-enum { LBM_MODEL_BGK = 0, LBM_MODEL_MRT = 1 };
+/* LBM_MODEL_COLOR names the two-fluid colour model, which has its own context
+ * (lbm_color_create below); lbm_create rejects it as an unknown model (LBM_EINVAL). */
+enum { LBM_MODEL_BGK = 0, LBM_MODEL_MRT = 1, LBM_MODEL_COLOR = 2 };
 
 /* Storage of the 19 distributions in device memory (arithmetic is FP64 for
  * LBM_PREC_FP64 and FP32 otherwise).  The 16-bit formats store the scaled
