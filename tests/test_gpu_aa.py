@@ -153,3 +153,37 @@ def test_aa_16bit_crosses_reference_refresh(torch_cuda, prec):
     assert abs(q16 - Q) <= 64 * 2.0 ** -bits * dmax * int((m[0] == 0).sum()) / 19
     assert np.abs(uz16 - uz32).max() <= 0.2 * np.abs(uz32).max() * (2.0 ** (11 - bits))
     assert abs(rin16 - rin32) <= 0.05 * abs(rin32 - 1)
+
+
+def test_aa_fp32_steady_duct_matches_poiseuille_series(torch_cuda):
+    """Section 3.1 on the benchmark's step: the 16x16x64 duct (tau = 1, mean inlet
+    velocity 1e-3) run on the AA pattern in FP32 until the Section 3.1 residual
+    is below 1e-6; the mid-plane profile matches the square-duct series with the
+    measured gradient (relative L2 error below 0.5 %, as the oracle at 2000
+    steps), and the flux through the mid-plane and the outlet equals Q to 0.1 %."""
+    import math
+
+    from paper_1806_10589_gb300 import Lattice, convergence as cv
+    from lbm_inputs import duct_mask
+
+    n, nz, tau = 16, 64, 1.0
+    m = duct_mask(n, n, nz)
+    Q = 1e-3 * (n - 2) ** 2
+    with Lattice(m, tau, "mrt", "fp32", stream=torch_cuda.cuda.current_stream()) as lat:
+        lat.set_kernel(3)
+        lat.set_flux_bc(Q)
+        r = cv.run_to_residual(lat, Q, tau, lag=500, tol=1e-6, max_steps=30000)
+        rho, ux, uy, uz = lat.fields()
+        q_out, _ = lat.get_flux(5)
+    assert r["converged"], r["residual"]
+    zs = np.arange(nz // 4, 3 * nz // 4)
+    rbar = np.array([rho[z][m[z] == 0].mean() for z in zs])
+    dpdz = O.CS2 * np.polyfit(zs, rbar, 1)[0]
+    c = np.arange(1, n - 1) - (n - 1) / 2.0
+    X, Y = np.meshgrid(c, c, indexing="xy")
+    th = O.duct_velocity(X, Y, (n - 2) / 2.0, O.CS2 * (tau - 0.5), dpdz)
+    sim = uz[nz // 2, 1:n - 1, 1:n - 1]
+    err = math.sqrt(((sim - th) ** 2).sum() / (th ** 2).sum())
+    assert err < 5e-3, err
+    assert abs(sim.sum() - Q) < 1e-3 * Q
+    assert abs(q_out - Q) < 1e-3 * Q
