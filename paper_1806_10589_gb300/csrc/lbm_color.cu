@@ -52,7 +52,6 @@ template <class T_>
 struct StoreIdent {
     using T = T_;
     using M = T_;
-    static constexpr bool kRef = false;
     template <int Q> __device__ static M dec(T v, M) { return v; }
     template <int Q> __device__ static T enc(M v, M) { return v; }
 };
