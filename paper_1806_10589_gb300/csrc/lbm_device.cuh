@@ -95,16 +95,18 @@ struct StoreF16 {
     using T = __half;
     using M = float;
     static constexpr bool kRef = true;
+    // one fused multiply-add each way; w r and 1024 r take few distinct values per
+    // node (3 weights, 3 planes), so the compiler forms them once
     template <int Q> __device__ static M dec(T v, M r) {
-        return float(wq(Q)) * fmaf(__half2float(v), 1.0f / 1024.0f, r);
+        return fmaf(__half2float(v), float(wq(Q) / 1024.0), float(wq(Q)) * r);
     }
     template <int Q> __device__ static T enc(M v, M r) {
-        return __float2half_rn(fmaf(v, float(1.0 / wq(Q)), -r) * 1024.0f);
+        return __float2half_rn(fmaf(v, float(1024.0 / wq(Q)), -1024.0f * r));
     }
     // FP32 keeps 13 more fraction bits than FP16: adding 13 random bits to the
     // magnitude and truncating rounds stochastically (FP16 normal range).
     template <int Q> __device__ static T enc_sr(M v, M r, uint32_t u) {
-        const float x = fmaf(v, float(1.0 / wq(Q)), -r) * 1024.0f;
+        const float x = fmaf(v, float(1024.0 / wq(Q)), -1024.0f * r);
         return __float2half_rz(__uint_as_float(__float_as_uint(x) + (u >> 19)));
     }
 };
@@ -113,14 +115,14 @@ struct StoreBF16 {
     using M = float;
     static constexpr bool kRef = true;
     template <int Q> __device__ static M dec(T v, M r) {
-        return float(wq(Q)) * fmaf(__bfloat162float(v), 1.0f / 1024.0f, r);
+        return fmaf(__bfloat162float(v), float(wq(Q) / 1024.0), float(wq(Q)) * r);
     }
     template <int Q> __device__ static T enc(M v, M r) {
-        return __float2bfloat16_rn(fmaf(v, float(1.0 / wq(Q)), -r) * 1024.0f);
+        return __float2bfloat16_rn(fmaf(v, float(1024.0 / wq(Q)), -1024.0f * r));
     }
     // BF16 is the upper half of FP32: add 16 random bits, then truncate.
     template <int Q> __device__ static T enc_sr(M v, M r, uint32_t u) {
-        const float x = fmaf(v, float(1.0 / wq(Q)), -r) * 1024.0f;
+        const float x = fmaf(v, float(1024.0 / wq(Q)), -1024.0f * r);
         return __float2bfloat16_rz(__uint_as_float(__float_as_uint(x) + (u >> 16)));
     }
 };

@@ -513,8 +513,15 @@ k_step_aa(const AAPtrs<typename S::T> F, int slot, DevLattice L, typename S::M s
                 constexpr int Q = decltype(qc)::value + 1;
                 nb[Q] = ld_aa_index(L.grid + (uint32_t)(p + (uint32_t)L.goff[Q]), pol_idx);
                 if constexpr (kIds == 2) sid[Q - 1][threadIdx.x] = nb[Q];
-                d[Q] = nb[Q] >= 0 ? S::template dec<Q>(F.row[opp(Q)][nb[Q]], r_own - M(cz(Q)) * g)
-                                  : S::template dec<Q>(F.row[Q][i], r_own);
+                if constexpr (S::kRef) {
+                    // 16-bit (instruction-bound): one load and one decode, the
+                    // source slot and its plane selected
+                    const bool pore = nb[Q] >= 0;
+                    const typename S::T* src = pore ? F.row[opp(Q)] + nb[Q] : F.row[Q] + i;
+                    d[Q] = S::template dec<Q>(*src, pore ? r_own - M(cz(Q)) * g : r_own);
+                } else {
+                    d[Q] = nb[Q] >= 0 ? F.row[opp(Q)][nb[Q]] : F.row[Q][i];
+                }
             });
         } else {
             if constexpr (S::kRef) r_own = own_ref<S>(bc, L, __ldg(L.vox + i));
@@ -546,9 +553,15 @@ k_step_aa(const AAPtrs<typename S::T> F, int slot, DevLattice L, typename S::M s
                 if constexpr (kIds == 1) dst = ld_aa_index(L.grid + (uint32_t)(ps + (uint32_t)L.goff[opp(Q)]), pol_s);
                 else if constexpr (kIds == 2) dst = sid[opp(Q) - 1][threadIdx.x];
                 else dst = nb[opp(Q)];
-                const uint32_t key = sr_key<S>(seed, i, Q);
-                if (dst >= 0) F.row[Q][dst] = S::template enc_sr<Q>(d[Q], r_own + M(cz(Q)) * g, key);
-                else F.row[opp(Q)][j] = S::template enc_sr<Q>(d[Q], r_own, key);
+                if constexpr (S::kRef) {
+                    // 16-bit: one encode and one store, destination slot and plane selected
+                    const bool pore = dst >= 0;
+                    typename S::T* out = pore ? F.row[Q] + dst : F.row[opp(Q)] + j;
+                    *out = S::template enc_sr<Q>(d[Q], pore ? r_own + M(cz(Q)) * g : r_own, sr_key<S>(seed, i, Q));
+                } else {  // FP32/FP64 store d directly; the branch form measured faster there
+                    if (dst >= 0) F.row[Q][dst] = d[Q];
+                    else F.row[opp(Q)][j] = d[Q];
+                }
             });
         } else {
             for_q(AllQ{}, [&](auto qc) {
