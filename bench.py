@@ -689,12 +689,26 @@ def run_warmstart(args):
 
 def run_profile_case(args):
     """Small, fixed launch sequence for ncu: create the benchmark lattice, W
-    single-step warm-up launches, then `steps` steps with per-launch events."""
+    single-step warm-up launches, then `steps` steps with per-launch events.
+    With --two-fluid-case: the two-fluid pack of the two-fluid leg instead
+    (gamma of its Laplace calibration, 0.0102), W + `steps` steps."""
     import torch
 
-    from paper_1806_10589_gb300 import Lattice
+    from paper_1806_10589_gb300 import ColorLattice, Lattice, drainage
 
     torch.cuda.set_device(0)
+    if args.two_fluid_case:
+        mask, info = sphere_pack((192, 192, 384), 5.0, 10.0, 0.35, seed=31, reservoir=6)
+        nz, ny, nx = mask.shape
+        Q = drainage.simulated_flux(1e-5, info["porosity"], nx * ny, 0.0102, drainage.lattice_viscosity(1.0))
+        with ColorLattice(mask, 1.0, 0.01, 0.95, -1.0, "fp32", stream=torch.cuda.current_stream()) as c:
+            zz = np.arange(nz)[:, None, None] * np.ones(mask.shape)
+            c.set_phase(np.where(zz < 6, 1.0, -1.0))
+            c.set_flux_bc(Q, 1.0)
+            c.step(args.warmup + args.steps)
+            torch.cuda.synchronize()
+        print(json.dumps({"profile_case": "two-fluid", "steps": args.warmup + args.steps}))
+        return
     mask, info, a_in = workload()
     variant = args.variant
     with Lattice(mask, TAU, "mrt", args.precision, stream=torch.cuda.current_stream()) as lat:
@@ -730,6 +744,8 @@ def main(argv=None):
     ap.add_argument("--ws-epochs", type=int, default=30)
     ap.add_argument("--ws-test", type=int, default=256)
     ap.add_argument("--ws-ref-steps", type=int, default=300000)
+    ap.add_argument("--two-fluid-case", action="store_true",
+                    help="with --profile-case: the two-fluid pack instead of the benchmark lattice")
     ap.add_argument("--profile-case", action="store_true",
                     help="run the short fixed launch sequence used for ncu captures")
     args = ap.parse_args(argv)
