@@ -190,6 +190,19 @@ __device__ __forceinline__ uint64_t l2_policy_evict_last() {
     asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
     return p;
 }
+// Bulk L2 prefetch (cp.async.bulk.prefetch.L2, sm_90 and later) of the elements
+// [s, min(s + len, end)) of an array that starts on a 16-byte boundary: the lines
+// are fetched into L2 in the background and nothing waits for them.  The caller
+// keeps s and end such that the byte offset and size are multiples of 16 (with
+// rows of ns elements, ns a multiple of 128, any s that is a multiple of 4).
+template <class T>
+__device__ __forceinline__ void l2_prefetch_range(const T* base, int64_t s, int64_t len, int64_t end) {
+    if (s < end) {
+        const int64_t e = s + len < end ? s + len : end;
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(__cvta_generic_to_global(base + s)),
+                     "r"((uint32_t)((e - s) * (int64_t)sizeof(T))));
+    }
+}
 __device__ __forceinline__ double ld_hint(const double* a, uint64_t pol) {
     double v;
     asm("ld.global.nc.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(a), "l"(pol));
