@@ -69,14 +69,42 @@ def workload():
 STEP_KERNEL_SOURCES = ("lbm_api.cu", "lbm_device.cuh", "lbm_internal.h", "lbm_kernels.cu")
 
 
+def strip_c_comments(src):
+    """C/C++ source without its // and /* */ comments (string and character
+    literals kept as they are); each comment leaves one space or its newline."""
+    out, i, n = [], 0, len(src)
+    while i < n:
+        c = src[i]
+        if c in "\"'":
+            j = i + 1
+            while j < n and src[j] != c:
+                j += 2 if src[j] == "\\" else 1
+            out.append(src[i:j + 1])
+            i = j + 1
+        elif src.startswith("//", i):
+            j = src.find("\n", i)
+            i = n if j < 0 else j
+        elif src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            out.append(" ")
+            i = n if j < 0 else j + 2
+        else:
+            out.append(c)
+            i += 1
+    return "".join(out)
+
+
 def kernel_sources_sha():
-    """Hash of the sources that define the single-lattice step kernel and its
-    launch (other modules of the library do not change it)."""
+    """Hash of the code (comments stripped, whitespace runs collapsed) of the
+    sources that define the single-lattice step kernel and its launch; other
+    modules of the library do not change it, and a comment or layout edit does
+    not invalidate a profile."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1806_10589_gb300", "csrc")
     for f in STEP_KERNEL_SOURCES:
-        with open(os.path.join(csrc, f), "rb") as fh:
-            h.update(f.encode() + b"\0" + fh.read())
+        with open(os.path.join(csrc, f), encoding="utf-8") as fh:
+            code = re.sub(r"\s+", " ", strip_c_comments(fh.read())).strip()
+            h.update(f.encode() + b"\0" + code.encode())
     return h.hexdigest()[:16]
 
 

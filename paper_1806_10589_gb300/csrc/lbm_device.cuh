@@ -193,8 +193,10 @@ __device__ __forceinline__ uint64_t l2_policy_evict_last() {
 // Bulk L2 prefetch (cp.async.bulk.prefetch.L2, sm_90 and later) of the elements
 // [s, min(s + len, end)) of an array that starts on a 16-byte boundary: the lines
 // are fetched into L2 in the background and nothing waits for them.  The caller
-// keeps s and end such that the byte offset and size are multiples of 16 (with
-// rows of ns elements, ns a multiple of 128, any s that is a multiple of 4).
+// keeps s and end multiples of 16 / sizeof(T) elements, so that the byte offset
+// and the size are multiples of 16 (a misaligned bulk copy is an illegal
+// instruction).  Rows of ns elements, ns a multiple of 128, keep any row start
+// aligned for every element size used here.
 template <class T>
 __device__ __forceinline__ void l2_prefetch_range(const T* base, int64_t s, int64_t len, int64_t end) {
     if (s < end) {
