@@ -48,9 +48,11 @@ def _f0(mask, seed, amp=0.01):
 
 
 def _run_pair(mask, tau, model, prec, steps, torch, Q=0.002, seed=3, inlet="flux", rho_in=1.0,
-              rho_out=1.0, amp=0.01, chunks=None):
+              rho_out=1.0, amp=0.01, chunks=None, variant=None):
     f0 = _f0(mask, seed, amp)
     with _lat(mask, tau, model, prec, torch) as lat:
+        if variant is not None:
+            lat.set_kernel(variant)
         if inlet == "flux":
             lat.set_flux_bc(Q)
         else:
@@ -204,15 +206,18 @@ def test_16bit_deviation_storage_error(torch_cuda, prec, bits):
     assert err <= bound, (err, bound)
 
 
-def test_full_size_sphere_pack_fp32_one_step(torch_cuda):
+@pytest.mark.parametrize("variant", [0, 3])
+def test_full_size_sphere_pack_fp32_one_step(torch_cuda, variant):
     """256^3 sphere pack (radii U[6,12], porosity 0.35, 6 reservoir layers), the
-    benchmark's FP32 configuration and launch shape, 2 steps from a seeded
-    perturbed state, all cells against the oracle."""
+    benchmark's FP32 configuration, 2 steps from a seeded perturbed state, all
+    cells against the oracle.  Variant 3 is the benchmark's launch shape (AA
+    pattern: layout swap, one gather-scatter and one node-local launch, swap
+    back); variant 0 the library default (two buffers)."""
     m, info = sphere_pack(256, 6, 12, 0.35, seed=2024, reservoir=6)
     A = int((m[0] == 0).sum())
     N = 2
     got, ref, (q_in, _), _ = _run_pair(m, 0.7, "mrt", "fp32", N, torch_cuda, Q=1e-4 * A, seed=77,
-                                       amp=0.001)
+                                       amp=0.001, variant=variant)
     d_ref = ref.f - O.W[:, None, None, None] * (m == 0)
     err = np.abs(got - ref.f).max()
     assert err <= 20 * N * EPS32 * np.abs(d_ref).max() + 4 * EPS32 * 1e-2, err
