@@ -119,6 +119,24 @@ def test_poiseuille_profile_duct16(duct16):
     assert dpdz < 0
 
 
+def test_darcy_permeability_of_the_duct(duct16):
+    """The time-to-steady rule's permeability (Darcy's law on the inlet density
+    of Eq. potential, u_D over the whole box face, length nz - 1) against the
+    Section 3.1 series: k = nu * (flow rate per unit gradient) / (nx ny) for the
+    14 x 14 pore cross-section (w = 7).  The oracle's steady duct gives it to
+    the profile's discretisation error (0.5 %); a wrong length (nz), area (pore
+    area), c_s^2 or viscosity is off by 2 % or far more."""
+    from paper_1806_10589_gb300 import convergence as cv
+
+    o, _, _, _, Q = duct16
+    nz, ny, nx = o.mask.shape
+    tau = 1.0
+    nu = O.CS2 * (tau - 0.5)
+    k_series = nu * O.duct_flow_rate_per_gradient(7.0, nu) / (nx * ny)
+    k = cv.permeability(Q, (nz, ny, nx), tau, o.rho_in, 1.0)
+    assert abs(k / k_series - 1.0) < 1e-2, (k, k_series)
+
+
 def test_duct_symmetry(duct16):
     _, sim, _, _, _ = duct16
     np.testing.assert_allclose(sim, sim.T, atol=1e-12 * sim.max())
