@@ -1,0 +1,81 @@
+"""Host helpers of the learned warm start (no GPU): the pore-solid face count
+of the Kozeny-Carman estimate against hand counts, the least-squares fit of
+its constant, and the seeded He initialisation's layout and spread."""
+import math
+
+import numpy as np
+
+from paper_1806_10589_gb300 import warmstart as ws
+
+
+def test_surface_density_open_box():
+    # all pore: only the four lateral box faces count (walls), the z ends do not
+    nz, ny, nx = 5, 4, 3
+    m = np.zeros((nz, ny, nx), np.uint8)
+    assert ws.surface_density(m) == (2 * nz * nx + 2 * nz * ny) / m.size
+
+
+def test_surface_density_one_interior_solid():
+    nz, ny, nx = 5, 5, 5
+    m = np.zeros((nz, ny, nx), np.uint8)
+    m[2, 2, 2] = 1
+    walls = 2 * nz * nx + 2 * nz * ny
+    assert ws.surface_density(m) == (walls + 6) / m.size
+
+
+def test_surface_density_all_solid_and_slab():
+    assert ws.surface_density(np.ones((3, 4, 5), np.uint8)) == 0.0
+    # a solid x-slab at x = 0 of a 4 x 3 x 6 box: it replaces the x = 0 wall by
+    # the slab's face toward x = 1 (same count), the y walls lose the slab's cells
+    nz, ny, nx = 4, 3, 6
+    m = np.zeros((nz, ny, nx), np.uint8)
+    m[:, :, 0] = 1
+    faces = nz * ny + nz * ny + 2 * nz * (nx - 1)
+    assert ws.surface_density(m) == faces / m.size
+
+
+def test_kc_features():
+    m = np.zeros((5, 5, 5), np.uint8)
+    m[2, 2, 2] = 1
+    phi, S, x = ws.kc_features(m)
+    assert phi == 124 / 125
+    assert S == ws.surface_density(m)
+    assert math.isclose(x, phi ** 3 / (S * S * (1 - phi) ** 2), rel_tol=1e-15)
+
+
+def test_fit_kc_recovers_the_constant():
+    rng = np.random.default_rng(3)
+    masks = [(rng.random((6, 6, 6)) < p).astype(np.uint8) for p in (0.2, 0.3, 0.4, 0.5)]
+    x = np.array([ws.kc_features(m)[2] for m in masks])
+    assert math.isclose(ws.fit_kc(masks, 0.37 * x), 0.37, rel_tol=1e-12)
+    # least squares in log k: multiplicative errors of +-10 % cancel in the geometric mean
+    noisy = 0.37 * x * np.array([1.1, 1 / 1.1, 1.1, 1 / 1.1])
+    assert math.isclose(ws.fit_kc(masks, noisy), 0.37, rel_tol=1e-12)
+
+
+class _Net:
+    def __init__(self, chans=(8, 16, 32)):
+        self.chans = chans
+        self.n_params = sum(co * ci * 27 + co for co, ci in self.layer_shapes())
+
+    def layer_shapes(self):
+        c0, c1, c2 = self.chans
+        return [(c0, 1), (c0, c0), (c1, c0), (c1, c1), (c2, c1), (c2, c2), (c1, c2), (c1, c1), (c0, c1),
+                (c0, c0), (3, c0)]
+
+
+def test_he_init_layout_and_spread():
+    net = _Net()
+    p = ws.he_init(net, 7)
+    assert p.dtype == np.float32 and p.size == net.n_params
+    np.testing.assert_array_equal(p, ws.he_init(net, 7))
+    k = 0
+    for co, ci in net.layer_shapes():
+        w = p[k:k + co * ci * 27]
+        b = p[k + co * ci * 27:k + co * ci * 27 + co]
+        assert not b.any()
+        target = math.sqrt(2.0 / (27 * ci))
+        # sample standard deviation of n normal draws: relative error ~ 1/sqrt(2n)
+        assert abs(w.std() / target - 1) < 5 / math.sqrt(2 * w.size)
+        k += co * ci * 27 + co
+    assert k == p.size
