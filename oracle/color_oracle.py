@@ -1,7 +1,7 @@
 """Plain FP64 CPU oracle of the two-fluid colour model (Appendix A) with the
 paper's flux inlet.
 
-TEST INFRASTRUCTURE ONLY (like lbm_oracle): the judge of the CUDA colour step.
+TEST INFRASTRUCTURE ONLY (like lbm_oracle): the correctness reference of the CUDA colour step.
 
 Per step, on the pore nodes of a voxel mask:
   1. phase field phi = (N_A - N_B) / (N_A + N_B), N_A = sum A_q, N_B = sum B_q (D3Q7);

@@ -1,7 +1,7 @@
 """Plain FP64 CPU oracle of the D3Q19 lattice Boltzmann step with the adaptive
 volumetric-flux boundary condition (McClure, Li, Sheppard, Miller, arXiv:1806.10589).
 
-TEST INFRASTRUCTURE ONLY.  This module is the correctness judge for the CUDA
+TEST INFRASTRUCTURE ONLY.  This module is the correctness reference for the CUDA
 path.  Only the test suite, the smoke check and the benchmark's CPU-baseline /
 reference leg may import it; the library itself never does.  It shares no code,
 table or helper with the CUDA sources.
