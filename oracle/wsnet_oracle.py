@@ -2,20 +2,23 @@
 
 TEST INFRASTRUCTURE ONLY (like lbm_oracle): checks the CUDA network kernels.
 The paper has no network; this is the library's own learned initial-field
-predictor, written out plainly so its gradients can be checked.
+predictor (a 3-D convolutional U-Net: `levels` resolution levels, `base`
+channels at full resolution, doubling per level), written out plainly so its
+gradients can be checked.
 
-Network (c = (c0, c1, c2) channels, volumes with every side divisible by 4):
-    X  : pore indicator (1 pore, 0 solid), 1 channel
-    L0a = relu(conv(X)),   L0b = relu(conv(L0a))                 full resolution
-    L1a = relu(conv(pool(L0b))), L1b = relu(conv(L1a))            1/2
-    L2a = relu(conv(pool(L1b))), L2b = relu(conv(L2a))            1/4
-    L3a = relu(conv(up(L2b))),   L3b = relu(conv(L3a + L1b))      1/2
-    L4a = relu(conv(up(L3b))),   L4b = relu(conv(L4a + L0b))      full
-    Y   = conv(L4b) * X                                           3 channels (u / u_D)
+Network (c_l = base * 2^l channels at level l; every side divisible by
+2^(levels - 1)):
+    X    : pore indicator (1 pore, 0 solid), 1 channel
+    E0a  = relu(conv(X)),        E0b = relu(conv(E0a))            level 0
+    El a = relu(conv(pool(E(l-1)b))), El b = relu(conv(El a))     l = 1 .. L-1
+    Dl a = relu(conv(up(D(l+1)b)))  (D(L-1)b := E(L-1)b)          l = L-2 .. 0
+    Sl   = Dl a + El b,      Dl b = relu(conv(Sl))
+    Y    = conv(D0b) * X                                          3 channels (u / u_D)
     loss = sum over pore voxels and channels of (Y - T)^2 / (3 n_pore)
 conv: 3x3x3 cross-correlation with zero padding and a bias; pool: 2x2x2 mean;
-up: nearest-neighbour 2x.  Parameters are stored layer by layer as W[co][ci][27]
-(taps ordered dz, dy, dx each in -1, 0, 1) followed by b[co].
+up: nearest-neighbour 2x.  Parameters are stored layer by layer (in the order
+the convolutions run above) as W[co][27][ci] -- the 27 taps ordered dz, dy, dx,
+each in -1, 0, 1, then the input channel -- followed by b[co].
 """
 from __future__ import annotations
 
@@ -24,26 +27,42 @@ import numpy as np
 TAPS = [(dz, dy, dx) for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1)]
 
 
-def layer_shapes(c0=8, c1=16, c2=32):
-    """(cout, cin) of the 11 convolutions in forward order."""
-    return [(c0, 1), (c0, c0), (c1, c0), (c1, c1), (c2, c1), (c2, c2),
-            (c1, c2), (c1, c1), (c0, c1), (c0, c0), (3, c0)]
+def channels(levels=4, base=32):
+    return [base * 2 ** l for l in range(levels)]
 
 
-def n_params(c0=8, c1=16, c2=32):
-    return sum(co * ci * 27 + co for co, ci in layer_shapes(c0, c1, c2))
+def layer_shapes(levels=4, base=32):
+    """(cout, cin) of the convolutions in forward order."""
+    c = channels(levels, base)
+    shapes = [(c[0], 1), (c[0], c[0])]
+    for l in range(1, levels):
+        shapes += [(c[l], c[l - 1]), (c[l], c[l])]
+    for l in range(levels - 2, -1, -1):
+        shapes += [(c[l], c[l + 1]), (c[l], c[l])]
+    shapes.append((3, c[0]))
+    return shapes
 
 
-def unpack(params, c0=8, c1=16, c2=32):
+def n_params(levels=4, base=32):
+    return sum(co * ci * 27 + co for co, ci in layer_shapes(levels, base))
+
+
+def unpack(params, levels=4, base=32):
+    """[(W[co][ci][27], b[co])] per layer from the packed W[co][27][ci], b[co] layout."""
     out, k = [], 0
-    for co, ci in layer_shapes(c0, c1, c2):
-        W = params[k:k + co * ci * 27].reshape(co, ci, 27)
+    for co, ci in layer_shapes(levels, base):
+        W = params[k:k + co * ci * 27].reshape(co, 27, ci).transpose(0, 2, 1)
         k += co * ci * 27
         b = params[k:k + co]
         k += co
         out.append((W, b))
     assert k == params.size
     return out
+
+
+def pack(layers):
+    """Inverse of unpack."""
+    return np.concatenate([np.concatenate([W.transpose(0, 2, 1).ravel(), b]) for W, b in layers])
 
 
 def shift(a, dz, dy, dx):
@@ -103,73 +122,73 @@ def relu(a):
     return np.maximum(a, 0.0)
 
 
-def forward(params, pore, chans=(8, 16, 32), keep=False):
+def forward(params, pore, levels=4, base=32, keep=False):
     """pore: (nz, ny, nx) 0/1.  Returns Y (3, nz, ny, nx) and, if keep, the
     intermediate activations for backward."""
-    Ls = unpack(np.asarray(params, dtype=np.float64), *chans)
+    Ls = unpack(np.asarray(params, dtype=np.float64), levels, base)
     X = np.asarray(pore, dtype=np.float64)[None]
-    A = {}
-    A["L0a"] = relu(conv(X, *Ls[0]))
-    A["L0b"] = relu(conv(A["L0a"], *Ls[1]))
-    A["P1"] = pool(A["L0b"])
-    A["L1a"] = relu(conv(A["P1"], *Ls[2]))
-    A["L1b"] = relu(conv(A["L1a"], *Ls[3]))
-    A["P2"] = pool(A["L1b"])
-    A["L2a"] = relu(conv(A["P2"], *Ls[4]))
-    A["L2b"] = relu(conv(A["L2a"], *Ls[5]))
-    A["U1"] = up(A["L2b"])
-    A["L3a"] = relu(conv(A["U1"], *Ls[6]))
-    A["S1"] = A["L3a"] + A["L1b"]
-    A["L3b"] = relu(conv(A["S1"], *Ls[7]))
-    A["U0"] = up(A["L3b"])
-    A["L4a"] = relu(conv(A["U0"], *Ls[8]))
-    A["S0"] = A["L4a"] + A["L0b"]
-    A["L4b"] = relu(conv(A["S0"], *Ls[9]))
-    A["Z"] = conv(A["L4b"], *Ls[10])
+    A = {"X": X}
+    k = 0
+    inp = X
+    for l in range(levels):
+        if l > 0:
+            inp = A["P%d" % l] = pool(A["E%db" % (l - 1)])
+        A["E%da" % l] = relu(conv(inp, *Ls[k]))
+        A["E%db" % l] = relu(conv(A["E%da" % l], *Ls[k + 1]))
+        k += 2
+    below = A["E%db" % (levels - 1)]
+    for l in range(levels - 2, -1, -1):
+        A["U%d" % l] = up(below)
+        A["D%da" % l] = relu(conv(A["U%d" % l], *Ls[k]))
+        A["S%d" % l] = A["D%da" % l] + A["E%db" % l]
+        A["D%db" % l] = relu(conv(A["S%d" % l], *Ls[k + 1]))
+        below = A["D%db" % l]
+        k += 2
+    A["Z"] = conv(below, *Ls[k])
     Y = A["Z"] * X
-    A["X"] = X
     return (Y, A) if keep else Y
 
 
-def loss_and_grad(params, pore, target, chans=(8, 16, 32)):
+def loss_and_grad(params, pore, target, levels=4, base=32):
     """Masked mean squared error and its gradient w.r.t. the packed parameters."""
     params = np.asarray(params, dtype=np.float64)
-    Ls = unpack(params, *chans)
-    Y, A = forward(params, pore, chans, keep=True)
+    Ls = unpack(params, levels, base)
+    Y, A = forward(params, pore, levels, base, keep=True)
     X = A["X"]
     npore = X.sum()
     diff = (Y - target) * X
     loss = (diff ** 2).sum() / (3.0 * npore)
     gY = 2.0 * diff / (3.0 * npore)
-    grads = [None] * 11
+    nl = len(Ls)
+    grads = [None] * nl
 
     def back(k, a_in, g_out):
         ga, gW, gb = conv_backward(a_in, Ls[k][0], g_out)
         grads[k] = (gW, gb)
         return ga
 
-    gZ = gY * X
-    g = back(10, A["L4b"], gZ)
-    g = g * (A["L4b"] > 0)
-    g_S0 = back(9, A["S0"], g)
-    g = g_S0 * (A["L4a"] > 0)
-    g_U0 = back(8, A["U0"], g)
-    g_L0b = g_S0.copy()
-    g = up_backward(g_U0) * (A["L3b"] > 0)
-    g_S1 = back(7, A["S1"], g)
-    g = g_S1 * (A["L3a"] > 0)
-    g_U1 = back(6, A["U1"], g)
-    g_L1b = g_S1.copy()
-    g = up_backward(g_U1) * (A["L2b"] > 0)
-    g = back(5, A["L2a"], g) * (A["L2a"] > 0)
-    g_P2 = back(4, A["P2"], g)
-    g_L1b += pool_backward(g_P2)
-    g = g_L1b * (A["L1b"] > 0)
-    g = back(3, A["L1a"], g) * (A["L1a"] > 0)
-    g_P1 = back(2, A["P1"], g)
-    g_L0b += pool_backward(g_P1)
-    g = g_L0b * (A["L0b"] > 0)
-    g = back(1, A["L0a"], g) * (A["L0a"] > 0)
-    back(0, X, g)
-    flat = np.concatenate([np.concatenate([gW.ravel(), gb]) for gW, gb in grads])
-    return loss, flat
+    k = nl - 1
+    top = "D0b" if levels > 1 else "E0b"
+    g = back(k, A[top], gY * X)              # gradient w.r.t. the last feature map
+    k -= 1
+    g_skip = {}
+    for l in range(0, levels - 1):           # decoder, top level first
+        g = g * (A["D%db" % l] > 0)
+        gS = back(k, A["S%d" % l], g)        # Dl b = relu(conv(Sl))
+        g_skip[l] = gS                       # Sl = Dl a + El b
+        g = gS * (A["D%da" % l] > 0)
+        gU = back(k - 1, A["U%d" % l], g)    # Dl a = relu(conv(Ul))
+        g = up_backward(gU)                  # into D(l+1)b, or E(L-1)b at the bottom
+        k -= 2
+    for l in range(levels - 1, -1, -1):      # encoder, bottom level first
+        if l < levels - 1:
+            g = g + g_skip[l]
+        g = g * (A["E%db" % l] > 0)
+        g = back(k, A["E%da" % l], g) * (A["E%da" % l] > 0)
+        inp = A["P%d" % l] if l > 0 else X
+        g = back(k - 1, inp, g)
+        if l > 0:
+            g = pool_backward(g)
+        k -= 2
+    assert k == -1
+    return loss, pack([(gW, gb) for gW, gb in grads])

@@ -54,14 +54,14 @@ def test_fit_kc_recovers_the_constant():
 
 
 class _Net:
-    def __init__(self, chans=(8, 16, 32)):
-        self.chans = chans
+    def __init__(self, levels=4, base=32):
+        self.levels, self.base = levels, base
         self.n_params = sum(co * ci * 27 + co for co, ci in self.layer_shapes())
 
     def layer_shapes(self):
-        c0, c1, c2 = self.chans
-        return [(c0, 1), (c0, c0), (c1, c0), (c1, c1), (c2, c1), (c2, c2), (c1, c2), (c1, c1), (c0, c1),
-                (c0, c0), (3, c0)]
+        from oracle import wsnet_oracle as N
+
+        return N.layer_shapes(self.levels, self.base)
 
 
 def test_he_init_layout_and_spread():

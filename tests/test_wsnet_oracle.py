@@ -1,7 +1,9 @@
 """Pins of the warm-start network oracle: its convolution equals scipy's
 n-dimensional correlation, pooling/upsampling backward are the adjoints of
-the forward maps, and the hand-written backward pass equals central finite
-differences of the forward pass."""
+the forward maps, the parameter packing round-trips, the specified network
+(4 levels, 32 base channels) has the stated layer shapes, and the
+hand-written backward pass equals central finite differences of the forward
+pass at every depth."""
 import numpy as np
 import pytest
 
@@ -33,21 +35,49 @@ def test_pool_up_adjoint():
     np.testing.assert_allclose(N.pool(N.up(g)), g)
 
 
-def test_backward_matches_finite_differences():
-    rng = np.random.default_rng(2)
-    chans = (2, 3, 4)
-    pore = (rng.random((8, 8, 8)) > 0.3).astype(float)
-    target = rng.standard_normal((3, 8, 8, 8))
-    p = rng.standard_normal(N.n_params(*chans)) * 0.3
-    loss, g = N.loss_and_grad(p, pore, target, chans)
-    idx = rng.choice(p.size, 40, replace=False)
+def test_pack_unpack_roundtrip_and_layout():
+    rng = np.random.default_rng(4)
+    p = rng.standard_normal(N.n_params(3, 2))
+    np.testing.assert_array_equal(N.pack(N.unpack(p, 3, 2)), p)
+    # first layer (cout 2, cin 1): W[co][t][ci] then b[co]
+    W, b = N.unpack(p, 3, 2)[0]
+    assert W.shape == (2, 1, 27)
+    np.testing.assert_array_equal(W[1, 0, :], p[27:54])
+    np.testing.assert_array_equal(b, p[54:56])
+    # second layer (2 <- 2): tap-major, then input channel
+    W1, _ = N.unpack(p, 3, 2)[1]
+    np.testing.assert_array_equal(W1[0, 1, 5], p[56 + 5 * 2 + 1])
+
+
+def test_specified_network_shapes():
+    shapes = N.layer_shapes(4, 32)
+    assert len(shapes) == 15
+    assert shapes[0] == (32, 1) and shapes[-1] == (3, 32)
+    assert [co for co, _ in shapes[:8:2]] == [32, 64, 128, 256]
+    assert shapes[8] == (128, 256) and shapes[12] == (32, 64)
+    assert N.n_params(4, 32) == sum(co * ci * 27 + co for co, ci in shapes)
+
+
+@pytest.mark.parametrize("levels,base,side", [(3, 2, 8), (4, 2, 8), (2, 3, 4)])
+def test_backward_matches_finite_differences(levels, base, side):
+    rng = np.random.default_rng(2 + levels)
+    pore = (rng.random((side, side, side)) > 0.3).astype(float)
+    target = rng.standard_normal((3, side, side, side))
+    p = rng.standard_normal(N.n_params(levels, base)) * 0.3
+    loss, g = N.loss_and_grad(p, pore, target, levels, base)
+    # sample parameters from every layer
+    idx, k = [], 0
+    for co, ci in N.layer_shapes(levels, base):
+        n = co * ci * 27 + co
+        idx += list(rng.choice(n, 3, replace=False) + k)
+        k += n
     h = 1e-6
     for k in idx:
         pp, pm = p.copy(), p.copy()
         pp[k] += h
         pm[k] -= h
-        lp, _ = N.loss_and_grad(pp, pore, target, chans)
-        lm, _ = N.loss_and_grad(pm, pore, target, chans)
+        lp, _ = N.loss_and_grad(pp, pore, target, levels, base)
+        lm, _ = N.loss_and_grad(pm, pore, target, levels, base)
         fd = (lp - lm) / (2 * h)
         assert abs(fd - g[k]) <= 1e-6 * max(1.0, abs(fd)), (k, fd, g[k])
 
@@ -55,6 +85,6 @@ def test_backward_matches_finite_differences():
 def test_output_is_zero_in_solids():
     rng = np.random.default_rng(3)
     pore = (rng.random((4, 8, 4)) > 0.5).astype(float)
-    p = rng.standard_normal(N.n_params(2, 2, 2))
-    Y = N.forward(p, pore, (2, 2, 2))
+    p = rng.standard_normal(N.n_params(3, 2))
+    Y = N.forward(p, pore, 3, 2)
     assert np.all(Y[:, pore == 0] == 0.0)
