@@ -682,7 +682,7 @@ def run_warmstart(args):
     torch.cuda.synchronize()
     t_lbm = time.perf_counter() - t0
     c_kc = ws.fit_kc(masks, ks)
-    net = WarmStartNet(8, 16, 32, stream=stream)
+    net = WarmStartNet(4, 32, stream=stream)
     net.set_params(ws.he_init(net, seed=4))
     ntr = int(0.9 * S)
     t0 = time.perf_counter()

@@ -175,10 +175,11 @@ int lbm_get_info(const lbm_ctx* ctx, int64_t* n_pore, int64_t* a_in, int64_t* a_
 int lbm_time_kernels(lbm_ctx* ctx, int n, float* ms_step_kernel, float* ms_inlet_kernel);
 
 /* Inlet density for callers that cannot allocate device memory at the point of
- * the call -- code inside a CUDA stream capture, where a cudaMalloc would break
- * the capture, or a process whose device memory is reserved up front by another
- * allocator.  The paper has no counterpart: this is a library-interface
- * addition.  It computes, from the context's current distributions and the
+ * the call -- a process whose device memory is reserved up front by another
+ * allocator (a framework's caching pool leaves no room for a second one), or
+ * real-time code that sizes all of its memory before it starts and must not
+ * stall in the allocator later.  The paper has no counterpart: this is a
+ * library-interface addition.  It computes, from the context's current distributions and the
  * prescribed Q, the inlet density rho_in of Eq. (potential) that the next step
  * imposes in flux mode, and writes it as one double to the caller-owned DEVICE
  * pointer rho_in_device, asynchronously on the context's stream.
@@ -189,7 +190,10 @@ int lbm_time_kernels(lbm_ctx* ctx, int n, float* ms_step_kernel, float* ms_inlet
  *   - Inlets of at most 524,288 pore nodes; larger ones return LBM_EINVAL.
  *   - All calls share the scratch array: calls whose kernels overlap on the GPU
  *     (other streams, other host threads, other contexts) race and must be
- *     serialised by the caller. */
+ *     serialised by the caller.
+ *   - The array's device address is cached per device for the life of the
+ *     process; after a cudaDeviceReset on that device the cached address is
+ *     stale, so the entry point must not be called there again. */
 int lbm_inlet_density_noalloc(lbm_ctx* ctx, double* rho_in_device);
 
 /* Free all device and host memory of the context.  NULL is accepted. */
@@ -315,19 +319,26 @@ int lbm_color_destroy(lbm_color* c);
 const char* lbm_color_last_error(const lbm_color* c);
 
 /* ---------------------------------------------------------------------------
- * Learned warm start (not in the paper; a library addition).  A small 3-D
- * U-Net (3 resolution levels with c0, c1, c2 channels, each in {8, 16, 32};
- * 3x3x3 convolutions, ReLU, 2x2x2 mean pooling, nearest upsampling, additive
- * skips) maps a voxel geometry to the steady velocity field divided by the
- * superficial velocity u_D = Q / (nx ny).  Forward, backward (data and weight
- * gradients) and Adam run in this library's CUDA kernels (FP32).  All volumes
- * have sides divisible by 4; masks are uint8 [z][y][x], 1 = solid (as for
- * lbm_create); fields are float32 [c][z][y][x] with c = u_x, u_y, u_z.
- * Parameters are stored layer by layer as W[cout][cin][27] (taps dz, dy, dx
- * each in -1, 0, 1) followed by b[cout]; they start at 0 until set.
+ * Learned warm start (not in the paper; a library addition).  A 3-D U-Net
+ * with `levels` resolution levels and base * 2^l channels at level l (the
+ * specified network: levels = 4, base = 32, i.e. 32/64/128/256 channels, 15
+ * convolutions; every channel count must be 32, 64, 128 or 256), 3x3x3
+ * convolutions, ReLU, 2x2x2 mean pooling, nearest upsampling and additive
+ * skips, maps a voxel geometry to the steady velocity field divided by the
+ * superficial velocity u_D = Q / (nx ny).  The convolutions (forward, data
+ * gradient, weight gradient) run on the tcgen05 tensor cores with BF16
+ * weights and activations and FP32 accumulation; pooling, upsampling, loss
+ * and Adam run in this library's CUDA kernels; the master parameters and Adam
+ * state are FP32.  All volumes have sides divisible by 2^(levels-1); masks are
+ * uint8 [z][y][x], 1 = solid (as for lbm_create); fields are float32
+ * [c][z][y][x] with c = u_x, u_y, u_z.  Parameters are stored layer by layer
+ * (forward order) as W[cout][27][cin] (taps dz, dy, dx each in -1, 0, 1, then
+ * the input channel) followed by b[cout]; they start at 0 until set.  A
+ * tensor-core pipeline wait that runs out (bounded at about one second)
+ * returns LBM_ETIMEOUT instead of hanging.
  * ------------------------------------------------------------------------- */
 typedef struct lbm_wsnet lbm_wsnet; /* opaque */
-int lbm_wsnet_create(int c0, int c1, int c2, lbm_wsnet** out);
+int lbm_wsnet_create(int levels, int base, lbm_wsnet** out);   /* LBM_EINVAL for an unsupported shape */
 int lbm_wsnet_num_params(const lbm_wsnet* net, int64_t* n);
 int lbm_wsnet_set_stream(lbm_wsnet* net, void* cuda_stream);
 int lbm_wsnet_set_params(lbm_wsnet* net, const float* params);   /* host, num_params floats; resets Adam */
@@ -345,10 +356,30 @@ int lbm_wsnet_train(lbm_wsnet* net, const uint8_t* masks, const float* targets, 
                     int nz, int epochs, int batch, float lr, const int* order, float* loss_history);
 /* Predicted u / u_D (host, 3*nz*ny*nx floats) of one geometry; 0 at solids. */
 int lbm_wsnet_predict(lbm_wsnet* net, const uint8_t* mask, int nx, int ny, int nz, float* y);
-/* Free the activation buffers kept between calls (they grow to the largest volume seen). */
+/* Free the activation buffers kept between calls (sized for the last batch and volume). */
 int lbm_wsnet_release_buffers(lbm_wsnet* net);
 int lbm_wsnet_destroy(lbm_wsnet* net);
 const char* lbm_wsnet_last_error(const lbm_wsnet* net);
+
+/* One 3x3x3 convolution of the network on the tensor cores, on caller-owned
+ * DEVICE buffers in the network's activation layout: BF16, channels last,
+ * [batch][nz+2][ny+2][nx+2][c] with a one-voxel border that must hold zeros
+ * (the layer's zero padding).  cin, cout in {32, 64, 128, 256}; w is BF16
+ * [cout][27][cin] (taps dz, dy, dx in -1..1).  Asynchronous work on `stream`,
+ * then a synchronisation of it.
+ *   op 0, forward:  out[v][co] = act(bias[co] + sum_t sum_ci w[co][t][ci] in[v + t][ci])
+ *         (in: cin channels; out: BF16, cout channels, border rows written 0;
+ *          bias FP32 [cout] or NULL; act = ReLU if relu, else identity)
+ *   op 1, data gradient:  out[v][ci] = sum_t sum_co w[co][t][ci] in[v - t][co]
+ *         (in: the output gradient, cout channels; out: BF16, cin channels,
+ *          border rows written 0)
+ *   op 2, weight gradient:  out[co][t][ci] += sum_v aux[v][co] in[v + t][ci]
+ *         (in: the layer input, cin channels; aux: the output gradient, cout
+ *          channels, zero on border rows; out: FP32 [cout][27][cin], added to)
+ * Returns LBM_EINVAL for bad arguments, LBM_ECUDA for a CUDA error and
+ * LBM_ETIMEOUT if a pipeline wait ran out. */
+int lbm_conv3d_bf16(int op, const void* in, const void* aux, const void* w, const float* bias, int relu, void* out,
+                    int batch, int nx, int ny, int nz, int cin, int cout, void* cuda_stream);
 
 #ifdef __cplusplus
 }

@@ -34,9 +34,10 @@ def sample(lat, Q, tau, rho_out=1.0):
     return {"k": permeability(Q, lat.shape, tau, rho_in, rho_out), "q_out": q_out, "rho_in": rho_in}
 
 
-def run_to_residual(lat, Q, tau, lag=1000, tol=1e-6, max_steps=400000, sync=None):
-    """Step until the Section 3.1 residual over `lag` steps is <= tol.
-    Returns dict(steps, seconds, residual, k, q_out, history)."""
+def run_to_residual(lat, Q, tau, lag=1000, tol=1e-6, max_steps=400000, sync=None, min_steps=0):
+    """Step until the Section 3.1 residual over `lag` steps is <= tol (and at
+    least `min_steps` steps have run).  Returns dict(steps, seconds, residual,
+    k, q_out, history)."""
     hist = []
     t0 = time.perf_counter()
     lat.steady_residual()
@@ -48,7 +49,7 @@ def run_to_residual(lat, Q, tau, lag=1000, tol=1e-6, max_steps=400000, sync=None
         r = lat.steady_residual()
         s = sample(lat, Q, tau)
         hist.append((steps, r, s["k"], s["q_out"]))
-        if r <= tol:
+        if r <= tol and steps >= min_steps:
             break
     if sync:
         sync()

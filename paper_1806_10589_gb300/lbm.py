@@ -85,7 +85,7 @@ SIGNATURES = {
     "lbm_color_get_flux": (C.c_int, [_P, C.c_int, _DP, _DP]),
     "lbm_color_destroy": (C.c_int, [_P]),
     "lbm_color_last_error": (C.c_char_p, [_P]),
-    "lbm_wsnet_create": (C.c_int, [C.c_int, C.c_int, C.c_int, C.POINTER(_P)]),
+    "lbm_wsnet_create": (C.c_int, [C.c_int, C.c_int, C.POINTER(_P)]),
     "lbm_wsnet_num_params": (C.c_int, [_P, _I64P]),
     "lbm_wsnet_set_stream": (C.c_int, [_P, _P]),
     "lbm_wsnet_set_params": (C.c_int, [_P, _FP]),
@@ -98,6 +98,8 @@ SIGNATURES = {
     "lbm_wsnet_release_buffers": (C.c_int, [_P]),
     "lbm_wsnet_destroy": (C.c_int, [_P]),
     "lbm_wsnet_last_error": (C.c_char_p, [_P]),
+    "lbm_conv3d_bf16": (C.c_int, [C.c_int, _P, _P, _P, _FP, C.c_int, _P, C.c_int, C.c_int, C.c_int, C.c_int,
+                                  C.c_int, C.c_int, _P]),
 }
 
 _lib = None
@@ -379,15 +381,17 @@ class Batch:
 
 
 class WarmStartNet:
-    """The warm-start network (lbm_wsnet_*)."""
+    """The warm-start network (lbm_wsnet_*): `levels` resolution levels with
+    base * 2^l channels at level l (the specified network: 4 levels, 32 base
+    channels)."""
 
-    def __init__(self, c0=8, c1=16, c2=32, stream=None):
+    def __init__(self, levels=4, base=32, stream=None):
         lib = load_library()
         h = _P()
-        st = lib.lbm_wsnet_create(int(c0), int(c1), int(c2), C.byref(h))
+        st = lib.lbm_wsnet_create(int(levels), int(base), C.byref(h))
         if st != LBM_OK:
-            raise LBMError(st, "lbm_wsnet_create(%d, %d, %d)" % (c0, c1, c2))
-        self._h, self._lib, self.chans = h, lib, (c0, c1, c2)
+            raise LBMError(st, "lbm_wsnet_create(%d, %d)" % (levels, base))
+        self._h, self._lib, self.levels, self.base = h, lib, int(levels), int(base)
         n = C.c_int64()
         self._check(lib.lbm_wsnet_num_params(h, C.byref(n)))
         self.n_params = n.value
@@ -411,10 +415,14 @@ class WarmStartNet:
             pass
 
     def layer_shapes(self):
-        """(cout, cin) of the 11 convolutions in the library's parameter order."""
-        c0, c1, c2 = self.chans
-        return [(c0, 1), (c0, c0), (c1, c0), (c1, c1), (c2, c1), (c2, c2), (c1, c2), (c1, c1), (c0, c1),
-                (c0, c0), (3, c0)]
+        """(cout, cin) of the convolutions in the library's parameter order."""
+        c = [self.base << l for l in range(self.levels)]
+        shapes = [(c[0], 1), (c[0], c[0])]
+        for l in range(1, self.levels):
+            shapes += [(c[l], c[l - 1]), (c[l], c[l])]
+        for l in range(self.levels - 2, -1, -1):
+            shapes += [(c[l], c[l + 1]), (c[l], c[l])]
+        return shapes + [(3, c[0])]
 
     def set_params(self, p):
         p = np.ascontiguousarray(p, dtype=np.float32)
@@ -458,6 +466,17 @@ class WarmStartNet:
 
     def release_buffers(self):
         self._check(self._lib.lbm_wsnet_release_buffers(self._h))
+
+
+def conv3d_bf16(op, inp, aux, w, bias, relu, out, batch, nx, ny, nz, cin, cout, stream=None):
+    """lbm_conv3d_bf16 on device pointers (ints, e.g. torch tensor.data_ptr())."""
+    lib = load_library()
+    hs = getattr(stream, "cuda_stream", stream) if stream is not None else None
+    st = lib.lbm_conv3d_bf16(int(op), _P(inp), _P(aux) if aux else None, _P(w),
+                             C.cast(_P(bias), _FP) if bias else None, int(relu), _P(out), int(batch), int(nx),
+                             int(ny), int(nz), int(cin), int(cout), _P(hs) if hs else None)
+    if st != LBM_OK:
+        raise LBMError(st, "lbm_conv3d_bf16(op %d, cin %d, cout %d)" % (op, cin, cout))
 
 
 class ColorLattice:

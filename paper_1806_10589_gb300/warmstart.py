@@ -82,39 +82,67 @@ def fit_kc(masks, ks):
     return float(np.exp(np.mean(np.log(ks) - np.log(x))))
 
 
-def initial_fields(net, mask, Q, tau, c_kc):
-    """(rho, ux, uy, uz) float64 arrays for Lattice.set_fields."""
+def initial_fields(net, mask, Q, tau, c_kc, use_net=True, use_ramp=True):
+    """(rho, ux, uy, uz) float64 arrays for Lattice.set_fields: u = u_D * net(mask)
+    (or 0 without the network), rho the Darcy / Kozeny-Carman ramp (or 1
+    without it)."""
     nz, ny, nx = mask.shape
     uD = Q / (nx * ny)
-    y = net.predict(mask).astype(np.float64) * uD
-    k_est = c_kc * kc_features(mask)[2]
-    nu = CS2 * (tau - 0.5)
-    dp = nu * uD * (nz - 1) / k_est
-    z = np.arange(nz, dtype=np.float64)[:, None, None]
-    rho = 1.0 + (dp / CS2) * (1.0 - z / (nz - 1)) + np.zeros(mask.shape)
+    if use_net:
+        y = net.predict(mask).astype(np.float64) * uD
+    else:
+        y = np.zeros((3,) + mask.shape)
+    rho = np.ones(mask.shape)
+    if use_ramp:
+        k_est = c_kc * kc_features(mask)[2]
+        nu = CS2 * (tau - 0.5)
+        dp = nu * uD * (nz - 1) / k_est
+        z = np.arange(nz, dtype=np.float64)[:, None, None]
+        rho = rho + (dp / CS2) * (1.0 - z / (nz - 1))
     return rho, y[0], y[1], y[2]
+
+
+# start name -> (network velocity, Kozeny-Carman density ramp)
+STARTS = {"cold": (False, False), "ramp_only": (False, True), "net_only": (True, False),
+          "net_and_ramp": (True, True)}
+
+
+def run_start(lattice_cls, net, mask, Q, tau, c_kc, k_ref, start, precision="fp32", stream=None, sync=None,
+              max_steps=400000, variant=0):
+    """Steps and wall seconds to the 0.1 % rule (k within 1e-3 of k_ref for 10
+    checks) from one of STARTS; the time of a warm start includes the network
+    inference and the field upload."""
+    use_net, use_ramp = STARTS[start]
+    with lattice_cls(mask, tau, "mrt", precision, stream=stream) as lat:
+        lat.set_kernel(variant)
+        lat.set_flux_bc(Q)
+        t_init = 0.0
+        if use_net or use_ramp:
+            if sync:
+                sync()
+            t0 = time.perf_counter()
+            rho, ux, uy, uz = initial_fields(net, mask, Q, tau, c_kc, use_net, use_ramp)
+            lat.set_fields(rho, ux, uy, uz)
+            if sync:
+                sync()
+            t_init = time.perf_counter() - t0
+        r = cv.run_to_reference(lat, Q, tau, k_ref, max_steps=max_steps, sync=sync)
+    return {"steps": r["steps"], "seconds": None if r["seconds"] is None else r["seconds"] + t_init,
+            "init_seconds": t_init, "reached": r["reached"], "k": r["k"], "q_out": r["q_out"],
+            "steps_run": r["steps_run"]}
 
 
 def warm_vs_cold(lattice_cls, net, mask, Q, tau, c_kc, k_ref, precision="fp32", stream=None, sync=None,
                  max_steps=400000, variant=0):
-    """Steps and wall seconds to the 0.1 % rule (k within 1e-3 for 10 checks)
-    from a cold start and from the learned warm start (the warm time includes
-    the network inference and the field upload), on step variant `variant`."""
-    out = {}
-    with lattice_cls(mask, tau, "mrt", precision, stream=stream) as lat:
-        lat.set_kernel(variant)
-        lat.set_flux_bc(Q)
-        r = cv.run_to_reference(lat, Q, tau, k_ref, max_steps=max_steps, sync=sync)
-        out["cold"] = {"steps": r["steps"], "seconds": r["seconds"], "reached": r["reached"], "k": r["k"],
-                       "q_out": r["q_out"]}
-    with lattice_cls(mask, tau, "mrt", precision, stream=stream) as lat:
-        lat.set_kernel(variant)
-        lat.set_flux_bc(Q)
-        t0 = time.perf_counter()
-        rho, ux, uy, uz = initial_fields(net, mask, Q, tau, c_kc)
-        lat.set_fields(rho, ux, uy, uz)
-        t_init = time.perf_counter() - t0
-        r = cv.run_to_reference(lat, Q, tau, k_ref, max_steps=max_steps, sync=sync)
-        out["warm"] = {"steps": r["steps"], "seconds": None if r["seconds"] is None else r["seconds"] + t_init,
-                       "init_seconds": t_init, "reached": r["reached"], "k": r["k"], "q_out": r["q_out"]}
-    return out
+    """The cold start and the full warm start (network velocity and ramp density)."""
+    args = (precision, stream, sync, max_steps, variant)
+    return {"cold": run_start(lattice_cls, net, mask, Q, tau, c_kc, k_ref, "cold", *args),
+            "warm": run_start(lattice_cls, net, mask, Q, tau, c_kc, k_ref, "net_and_ramp", *args)}
+
+
+def ablation(lattice_cls, net, mask, Q, tau, c_kc, k_ref, precision="fp32", stream=None, sync=None,
+             max_steps=400000, variant=0):
+    """All four starts (cold, ramp only, network only, both) to the 0.1 % rule:
+    what the network adds over the analytic ramp, and the ramp over nothing."""
+    return {name: run_start(lattice_cls, net, mask, Q, tau, c_kc, k_ref, name, precision, stream, sync,
+                            max_steps, variant) for name in STARTS}

@@ -1,92 +1,203 @@
-"""GPU checks of the warm-start network kernels (lbm_wsnet_*) against the FP64
-numpy oracle: forward output, masked MSE loss and every parameter gradient.
+"""GPU checks of the warm-start network against the FP64 numpy oracle.
 
-Tolerance: the CUDA path computes in FP32 with atomically accumulated weight
-gradients, the oracle in FP64; with O(1) activations and ~10^3-term sums the
-FP32 error is ~1e-5 of the largest value, so forward and gradients are
-compared at 2e-4 of their maximum magnitude and the loss at 1e-5 relative."""
+Single convolutions (lbm_conv3d_bf16: forward, data gradient, weight
+gradient) on the tensor cores, for channel pairs covering every operand
+shape and swizzle mode, on a ragged multi-tile volume.  Inputs and weights are
+rounded to BF16 on the host and the oracle gets the same rounded values, so
+the only differences are in the arithmetic: the products of two BF16 values
+are exact in FP32; each FP32 addition rounds by at most 2^-24 of the running
+sum, whose magnitude is at most S = the same sum over absolute values; the
+forward and data-gradient outputs are then rounded to BF16 (2^-8 relative,
+half an ulp of 8 significant bits, times two for the rounding of the sum
+before it).  Allowing 2^8 rounding steps on the path of one sum gives
+|got - ref| <= 2^-8 |ref| + 2^-16 S.
+
+The whole network (4 levels, 32 base channels): loss and every parameter
+gradient against the FP64 oracle.  Here BF16 rounds every activation and
+gradient tensor (relative 2^-9) on a path of about 30 layers forward and
+back, and a rounding can move a ReLU input across zero; the test states the
+per-layer relative L2 error of the gradient at <= 0.06 and the loss at 1e-2."""
 import numpy as np
 import pytest
 
 from oracle import wsnet_oracle as N
 
 pytestmark = pytest.mark.gpu
-CH = (8, 16, 32)
 
 
 @pytest.fixture(scope="module")
-def net():
-    torch = pytest.importorskip("torch")
-    if not torch.cuda.is_available():
+def torch():
+    t = pytest.importorskip("torch")
+    if not t.cuda.is_available():
         pytest.skip("no CUDA device")
-    torch.cuda.set_device(0)
+    t.cuda.set_device(0)
     import __graft_entry__
 
     __graft_entry__.build()
+    return t
+
+
+def _bf16(torch, a):
+    return torch.tensor(np.asarray(a, np.float32)).to(torch.bfloat16)
+
+
+def _padded(torch, x):
+    """[B][C][Z][Y][X] float -> device BF16 [B][Z+2][Y+2][X+2][C] with a zero border,
+    and the BF16-rounded values as float64 (same shape as x)."""
+    B, C, Z, Y, X = x.shape
+    t = torch.zeros((B, Z + 2, Y + 2, X + 2, C), dtype=torch.bfloat16, device="cuda")
+    xb = _bf16(torch, x)
+    t[:, 1:-1, 1:-1, 1:-1, :] = xb.permute(0, 2, 3, 4, 1).cuda()
+    return t, xb.double().numpy()
+
+
+def _unpad(t):
+    return t[:, 1:-1, 1:-1, 1:-1, :].permute(0, 4, 1, 2, 3).double().cpu().numpy()
+
+
+PAIRS = [(32, 32), (32, 64), (64, 32), (64, 128), (128, 256), (256, 128), (256, 256), (32, 256)]
+SHAPE = (2, 6, 7, 9)  # B, Z, Y, X: 2 * 8 * 9 * 11 padded rows = 13 tiles of 128 with a ragged tail
+
+
+@pytest.mark.parametrize("cin,cout", PAIRS)
+def test_conv_layer_matches_oracle(torch, cin, cout):
+    from paper_1806_10589_gb300 import conv3d_bf16
+
+    B, Z, Y, X = SHAPE
+    rng = np.random.default_rng(cin * 7 + cout)
+    a = rng.standard_normal((B, cin, Z, Y, X))
+    g = rng.standard_normal((B, cout, Z, Y, X))
+    w = rng.standard_normal((cout, 27, cin)) / np.sqrt(27 * cin)
+    bias = rng.standard_normal(cout).astype(np.float32)
+    ta, a_r = _padded(torch, a)
+    tg, g_r = _padded(torch, g)
+    wb = _bf16(torch, w)
+    w_r = wb.double().numpy().transpose(0, 2, 1)          # oracle layout W[co][ci][27]
+    tw = wb.cuda().contiguous()
+    tb = torch.tensor(bias).cuda()
+    st = torch.cuda.current_stream()
+
+    # forward with ReLU
+    out = torch.full((B, Z + 2, Y + 2, X + 2, cout), 7.0, dtype=torch.bfloat16, device="cuda")
+    conv3d_bf16(0, ta.data_ptr(), 0, tw.data_ptr(), tb.data_ptr(), 1, out.data_ptr(), B, X, Y, Z, cin, cout, st)
+    got = _unpad(out)
+    border = out.clone()
+    border[:, 1:-1, 1:-1, 1:-1, :] = 0
+    assert not border.any(), "border rows must be written 0"
+    for b in range(B):
+        ref = N.relu(N.conv(a_r[b], w_r, bias.astype(np.float64)))
+        S = N.conv(np.abs(a_r[b]), np.abs(w_r), np.abs(bias.astype(np.float64)))
+        err = np.abs(got[b] - ref) - (2.0 ** -8 * np.abs(ref) + 2.0 ** -16 * S)
+        assert err.max() <= 0, ("forward", b, float(err.max()), float(np.abs(ref).max()))
+
+    # data gradient
+    gin = torch.full((B, Z + 2, Y + 2, X + 2, cin), 7.0, dtype=torch.bfloat16, device="cuda")
+    conv3d_bf16(1, tg.data_ptr(), 0, tw.data_ptr(), 0, 0, gin.data_ptr(), B, X, Y, Z, cin, cout, st)
+    got = _unpad(gin)
+    for b in range(B):
+        ref, _, _ = N.conv_backward(a_r[b], w_r, g_r[b])
+        S, _, _ = N.conv_backward(np.abs(a_r[b]), np.abs(w_r), np.abs(g_r[b]))
+        err = np.abs(got[b] - ref) - (2.0 ** -8 * np.abs(ref) + 2.0 ** -16 * S)
+        assert err.max() <= 0, ("data gradient", b, float(err.max()), float(np.abs(ref).max()))
+
+    # weight gradient (accumulated onto a preset value)
+    gw = torch.full((cout, 27, cin), 0.5, dtype=torch.float32, device="cuda")
+    conv3d_bf16(2, ta.data_ptr(), tg.data_ptr(), tw.data_ptr(), 0, 0, gw.data_ptr(), B, X, Y, Z, cin, cout, st)
+    got = gw.double().cpu().numpy().transpose(0, 2, 1) - 0.5
+    ref = np.zeros((cout, cin, 27))
+    S = np.zeros((cout, cin, 27))
+    for b in range(B):
+        ref += N.conv_backward(a_r[b], w_r, g_r[b])[1]
+        S += N.conv_backward(np.abs(a_r[b]), np.abs(w_r), np.abs(g_r[b]))[1]
+    err = np.abs(got - ref) - (2.0 ** -16 * S + 2.0 ** -22)
+    assert err.max() <= 0, ("weight gradient", float(err.max()), float(np.abs(ref).max()))
+
+
+def test_conv_rejects_bad_shapes(torch):
+    from paper_1806_10589_gb300 import LBMError, conv3d_bf16
+
+    with pytest.raises(LBMError):
+        conv3d_bf16(0, 1, 0, 1, 0, 0, 1, 1, 4, 4, 4, 48, 32)
+    with pytest.raises(LBMError):
+        conv3d_bf16(2, 1, 0, 1, 0, 0, 1, 1, 4, 4, 4, 32, 32)  # weight gradient needs the output gradient
+
+
+@pytest.fixture(scope="module")
+def net(torch):
     from paper_1806_10589_gb300 import WarmStartNet
 
-    n = WarmStartNet(*CH)
+    n = WarmStartNet(4, 32, stream=torch.cuda.current_stream())
     yield n
     n.close()
 
 
-def _case(seed, B=2, shape=(8, 12, 8)):
+def _he(n_levels, base, seed):
     rng = np.random.default_rng(seed)
-    masks = (rng.random((B,) + shape) < 0.35).astype(np.uint8)
-    targets = rng.standard_normal((B, 3) + shape).astype(np.float32)
-    params = (rng.standard_normal(N.n_params(*CH)) * 0.15).astype(np.float32)
-    return masks, targets, params
+    parts = []
+    for co, ci in N.layer_shapes(n_levels, base):
+        parts.append(rng.standard_normal(co * 27 * ci) * np.sqrt(2.0 / (27 * ci)))
+        parts.append(0.05 * rng.standard_normal(co))
+    return np.concatenate(parts).astype(np.float32)
 
 
 def test_param_count(net):
-    assert net.n_params == N.n_params(*CH)
+    assert net.n_params == N.n_params(4, 32)
+    assert net.layer_shapes() == N.layer_shapes(4, 32)
 
 
 def test_forward_matches_oracle(net):
-    masks, _, p = _case(1, B=1)
+    rng = np.random.default_rng(1)
+    mask = (rng.random((16, 8, 8)) < 0.35).astype(np.uint8)
+    p = _he(4, 32, 11)
     net.set_params(p)
-    y = net.predict(masks[0])
-    ref = N.forward(p.astype(np.float64), 1.0 - masks[0], CH)
-    assert np.abs(y - ref).max() <= 2e-4 * max(1.0, np.abs(ref).max())
-    assert np.all(y[:, masks[0] == 1] == 0)
+    y = net.predict(mask)
+    ref = N.forward(p.astype(np.float64), 1.0 - mask, 4, 32)
+    assert np.all(y[:, mask == 1] == 0)
+    rel = np.linalg.norm(y - ref) / np.linalg.norm(ref)
+    assert rel <= 0.03, rel
 
 
 def test_loss_and_gradient_match_oracle(net):
-    masks, targets, p = _case(2)
+    rng = np.random.default_rng(2)
+    B, shape = 2, (16, 8, 8)
+    masks = (rng.random((B,) + shape) < 0.35).astype(np.uint8)
+    targets = rng.standard_normal((B, 3) + shape).astype(np.float32)
+    p = _he(4, 32, 12)
     net.set_params(p)
     loss, g = net.loss_grad(masks, targets)
-    # the oracle's loss is per sample; a batch of B shares one normalisation by
-    # the total pore count, so sum the per-sample parts with that weight
+    # one normalisation by the batch's total pore count
     npore = float((masks == 0).sum())
     ref_loss, ref_g = 0.0, np.zeros(p.size)
-    for b in range(masks.shape[0]):
+    for b in range(B):
         nb = float((masks[b] == 0).sum())
-        lb, gb = N.loss_and_grad(p.astype(np.float64), 1.0 - masks[b], targets[b], CH)
+        lb, gb = N.loss_and_grad(p.astype(np.float64), 1.0 - masks[b], targets[b], 4, 32)
         ref_loss += lb * nb / npore
         ref_g += gb * nb / npore
-    assert abs(loss - ref_loss) <= 1e-5 * ref_loss
-    assert np.abs(g - ref_g).max() <= 2e-4 * np.abs(ref_g).max()
+    assert abs(loss - ref_loss) <= 1e-2 * ref_loss, (loss, ref_loss)
+    k = 0
+    for li, (co, ci) in enumerate(N.layer_shapes(4, 32)):
+        n = co * 27 * ci + co
+        a, r = g[k:k + n], ref_g[k:k + n]
+        rel = np.linalg.norm(a - r) / max(np.linalg.norm(r), 1e-30)
+        assert rel <= 0.06, (li, co, ci, rel)
+        k += n
 
 
 def test_training_reduces_loss(net):
     rng = np.random.default_rng(5)
     masks = (rng.random((6, 8, 8, 8)) < 0.3).astype(np.uint8)
-    # a learnable target: a smooth function of the local pore fraction
     pore = 1.0 - masks.astype(np.float32)
     t = np.stack([pore * 0.5, pore * -0.2, pore * (1.0 + 0.1 * np.arange(8)[None, :, None, None])], axis=1)
-    p = (rng.standard_normal(net.n_params) * 0.1).astype(np.float32)
-    net.set_params(p)
-    hist = net.train(masks, t.astype(np.float32), epochs=60, batch=3, lr=3e-3, seed=1)
+    net.set_params(_he(4, 32, 3) * 0.5)
+    hist = net.train(masks, t.astype(np.float32), epochs=60, batch=3, lr=1e-3, seed=1)
     assert np.isfinite(hist).all()
     assert hist[-1] < 0.2 * hist[0], hist[[0, -1]]
 
 
-def test_warm_start_pipeline_small(net):
+def test_warm_start_pipeline_small(net, torch):
     """End to end at small scale: steady targets from the batched LBM, a short
     training run, Kozeny-Carman calibration and a warm-started lattice that
     reaches the 0.1 % rule of a reference run."""
-    import torch
-
     from lbm_inputs import sphere_pack
     from paper_1806_10589_gb300 import Batch, Lattice, convergence as cv, warmstart as ws
 
