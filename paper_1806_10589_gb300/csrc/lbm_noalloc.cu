@@ -1,12 +1,13 @@
 // Inlet density without any device allocation (lbm_inlet_density_noalloc).
 //
 // Some callers cannot let the library call cudaMalloc at the moment they need
-// this value: code running inside a CUDA stream capture (an allocation would
-// invalidate the capture), or processes whose device memory is fully reserved
-// by another allocator (e.g. a framework's caching pool) or sized up front for
-// real-time use.  For them, the inlet reduction below keeps its per-block
-// partial sums and its ticket counter in a file-scope static device array of
-// fixed size instead of in memory allocated per context or per call.
+// this value: processes whose device memory is fully reserved by another
+// allocator (e.g. a framework's caching pool, where a second allocator would
+// find no room), or real-time code that sizes all of its memory up front and
+// must not stall in the allocator later.  For them, the inlet reduction below
+// keeps its per-block partial sums and its ticket counter in a file-scope
+// static device array of fixed size instead of in memory allocated per
+// context or per call.
 //
 // The array belongs to the loaded library: every GPU that loads it holds
 // kNoAllocScratchDoubles * 8 bytes until the process exits.  All calls share it
@@ -40,7 +41,10 @@ double* g_scratch_ptr[kMaxDevices] = {};
 
 // Device address of g_noalloc_scratch on the current device.  In host code the
 // symbol's name is only a host-side handle, never a device address, so it is
-// looked up once per device (with that device current) and cached.
+// looked up once per device (with that device current) and cached.  The cached
+// address belongs to the device context that was current at the lookup: after
+// a cudaDeviceReset on that device it is stale, and the entry point must not
+// be called again in that process.
 cudaError_t scratch_on_current_device(double** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
