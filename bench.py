@@ -45,6 +45,7 @@ TAU = 0.7
 UBAR = 1e-4
 BYTES_PER_VALUE = {"fp64": 8, "fp32": 4, "fp16dev": 2, "bf16dev": 2}
 FALLBACK_HBM_GBS = 6800.0
+NOMINAL_HBM_GBS = 8000.0  # the ~8 TB/s nominal HBM3e peak (the measured copy bandwidth is the roofline)
 PROFILE_TRAFFIC = {0: os.path.join(ROOT, "profiles", "k_step_fp32_sphere256.md"),
                    3: os.path.join(ROOT, "profiles", "k_step_aa_fp32_sphere256.md")}
 VARIANT_NAMES = {0: "per-node pull kernel, two buffers", 1: "cp.async-pipelined, 256-node tiles",
@@ -119,6 +120,20 @@ def measured_hbm_peak():
     except (OSError, ValueError):
         pass
     return FALLBACK_HBM_GBS, "fallback"
+
+
+def measured_bf16_peak():
+    """Dense BF16 tensor throughput (TFLOP/s) for a kernel timed alone: the
+    burst cuBLAS figure of MEASURED_PEAKS.json, else the fallback."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as fh:
+            d = json.load(fh)
+        if d.get("bf16_tflops"):
+            return float(d["bf16_tflops"]), "measured (MEASURED_PEAKS.json bf16_tflops, burst)"
+    except (OSError, ValueError):
+        pass
+    return 1900.0, "fallback 1.9 PFLOP/s"
 
 
 def profiled_traffic(sha, variant=0):
@@ -207,37 +222,105 @@ print(json.dumps({"seconds": dt, "n_pore": int((m == 0).sum()), "steps": steps})
 """
 
 
-def oracle_rate(mask, steps, tau=TAU, ubar=UBAR):
-    """Run the FP64 CPU oracle on `mask` in a single-threaded child process;
-    return (MLUPS, seconds, n_pore)."""
-    a_in = int((mask[0] == 0).sum())
+def _oracle_env():
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
         env[k] = "1"
+    return env
+
+
+def oracle_rate(mask, steps, tau=TAU, ubar=UBAR):
+    """Run the FP64 CPU oracle on `mask` in a single-threaded child process;
+    return (MLUPS, seconds, n_pore)."""
+    r = oracle_rate_parallel([mask], steps, tau, ubar)
+    return r["mlups"], r["seconds"], r["n_pore"]
+
+
+def oracle_rate_parallel(masks, steps, tau=TAU, ubar=UBAR):
+    """Run one single-threaded FP64 oracle child process per mask, all at the
+    same time (one per host core); aggregate MLUPS = all children's pore-node
+    updates over the longest child's timed region."""
     with tempfile.TemporaryDirectory() as td:
-        p = os.path.join(td, "mask.npy")
-        np.save(p, mask)
-        r = subprocess.run([sys.executable, "-c", ORACLE_CHILD, ROOT, p, str(steps), str(tau),
-                            repr(ubar * a_in)], capture_output=True, text=True, env=env)
-    if r.returncode != 0:
-        raise RuntimeError("oracle child failed: " + r.stderr[-2000:])
-    d = json.loads(r.stdout.strip().splitlines()[-1])
-    return d["n_pore"] * d["steps"] / d["seconds"] / 1e6, d["seconds"], d["n_pore"]
+        procs = []
+        for j, m in enumerate(masks):
+            p = os.path.join(td, "mask%d.npy" % j)
+            np.save(p, m)
+            a_in = int((m[0] == 0).sum())
+            procs.append(subprocess.Popen([sys.executable, "-c", ORACLE_CHILD, ROOT, p, str(steps), str(tau),
+                                           repr(ubar * a_in)], stdout=subprocess.PIPE, stderr=subprocess.PIPE,
+                                          text=True, env=_oracle_env()))
+        res = []
+        for pr in procs:
+            out, err = pr.communicate()
+            if pr.returncode != 0:
+                raise RuntimeError("oracle child failed: " + err[-2000:])
+            res.append(json.loads(out.strip().splitlines()[-1]))
+    secs = max(d["seconds"] for d in res)
+    n = sum(d["n_pore"] for d in res)
+    return {"mlups": n * steps / secs / 1e6, "seconds": secs, "n_pore": n, "children": len(res)}
 
 
-def crop_for_budget(mask, seconds_per_step, probe_mlups):
-    """A z-slab of the pack (inlet side, full x/y extent shrunk if needed) whose
-    oracle step takes about `seconds_per_step`."""
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
+def host_cpu_model():
+    try:
+        r = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10)
+        for line in r.stdout.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return "unknown"
+
+
+def host_mem_available():
+    try:
+        for line in open("/proc/meminfo"):
+            if line.startswith("MemAvailable:"):
+                return int(line.split()[1]) * 1024
+    except OSError:
+        pass
+    return 16 << 30
+
+
+def crop_for_budget(mask, seconds_per_step, probe_mlups, z0=0, max_cells=None):
+    """A z-slab of the pack starting at plane z0 (full x/y extent, shrunk if
+    needed) whose oracle step takes about `seconds_per_step`."""
     nz, ny, nx = mask.shape
     phi = float((mask == 0).mean())
     cells = max(seconds_per_step * probe_mlups * 1e6 / phi, 4 * 4 * 3)
+    if max_cells:
+        cells = min(cells, max_cells)
     if cells >= nx * ny * 3:
         dz = int(min(nz, max(3, cells // (nx * ny))))
-        return mask[:dz].copy()
-    side = int(max(4, min(nx, (cells / 3) ** 0.5)))
-    sub = mask[:3, :side, :side].copy()
-    sub[0][sub[0] == 1] = 0  # keep inlet/outlet pores in a tiny sample
+        z0 = max(0, min(z0, nz - dz))
+        sub = mask[z0:z0 + dz].copy()
+    else:
+        side = int(max(4, min(nx, (cells / 3) ** 0.5)))
+        z0 = max(0, min(z0, nz - 3))
+        sub = mask[z0:z0 + 3, :side, :side].copy()
+    for zz in (0, -1):  # the flux inlet and the pressure outlet need pores on their planes
+        if not (sub[zz] == 0).any():
+            sub[zz] = 0
     return sub
+
+
+def oracle_samples(mask, seconds_per_step, probe_mlups, cores):
+    """One z-slab of the pack per core, spread over the whole depth (slabs may
+    overlap; each is an independent problem), sized for `seconds_per_step` of
+    single-core oracle time per step and for the host memory left."""
+    budget_cells = 0.25 * host_mem_available() / max(1, cores) / 2000.0  # ~2 kB of oracle arrays per cell
+    nz = mask.shape[0]
+    out = []
+    for j in range(cores):
+        z0 = int(round(j * max(0, nz - 3) / max(1, cores - 1))) if cores > 1 else 0
+        out.append(crop_for_budget(mask, seconds_per_step, probe_mlups, z0=z0, max_cells=budget_cells))
+    return out
 
 
 def aggregate(n_local, K, ms_local, world, device=None):
@@ -257,38 +340,86 @@ def aggregate(n_local, K, ms_local, world, device=None):
     return total * K / (ms * 1e-3) / 1e6, ms
 
 
-def time_to_steady(mask, a_in, stream, max_steps=150000, variant=3, precs=("fp32", "fp16dev", "bf16dev")):
-    """Cold-start runs to steady flux on the benchmark workload, all on step
-    variant `variant`: the FP32 reference k_inf by the Section 3.1 rule
-    (residual over 1000 steps <= 1e-6), then FP32 / FP16-dev / BF16-dev cold runs
-    until k(t) is within 0.1 % of k_inf for 10 consecutive checks (every 100
-    steps).  Wall times include the checks."""
+def velocity_errors(u, u_ref, pore):
+    """Relative L2 error of the velocity over pore nodes, and the largest
+    absolute error (also relative to the largest reference speed)."""
+    du = np.stack([a[pore] - b[pore] for a, b in zip(u, u_ref)])
+    ref = np.stack([b[pore] for b in u_ref])
+    n_ref = float(np.sqrt((ref ** 2).sum()))
+    mx = float(np.abs(du).max())
+    return {"u_l2_rel": float(np.sqrt((du ** 2).sum())) / n_ref, "u_max_abs": mx,
+            "u_max_rel": mx / float(np.abs(ref).max())}
+
+
+def error_block(lat, Q, k_ref, q_ref, u_ref, pore):
+    from paper_1806_10589_gb300 import convergence as cv
+
+    s = cv.sample(lat, Q, TAU)
+    _, ux, uy, uz = lat.fields()
+    out = {"k_rel": (s["k"] - k_ref) / k_ref, "q_out_rel": (s["q_out"] - q_ref) / Q}
+    out.update(velocity_errors((ux, uy, uz), u_ref, pore))
+    return out
+
+
+def time_to_steady(mask, a_in, stream, max_steps=150000, variant=3, precs=("fp32", "fp16dev", "bf16dev"),
+                   bias_steps=10000):
+    """Time to steady flux on the benchmark workload, all on step variant
+    `variant`, against an FP64 reference:
+      1. FP32 cold run to the Section 3.1 rule (residual over 1000 steps <= 1e-6);
+      2. the FP64 GPU path (pinned to the FP64 oracle at 1e-11) from that state's
+         distributions, to the same rule and at least 6000 steps: k_inf, Q_out and
+         u of FP64;
+      3. FP32 / FP16-dev / BF16-dev cold runs until k(t) is within 0.1 % of the
+         FP64 k_inf for 10 consecutive checks (every 100 steps); wall times include
+         the checks; k, Q_out and u errors against FP64 when the rule is met;
+      4. each format started from the FP64 steady state and run `bias_steps`
+         steps: its steady-state error against FP64."""
     import torch
 
     from paper_1806_10589_gb300 import Lattice, convergence as cv
 
     Q = UBAR * a_in
-    out = {"criterion": "k within 0.1% of k_inf for 10 consecutive checks (every 100 steps); "
-                        "k_inf: FP32 cold run to sum|u(t)-u(t-1000)|/sum|u| <= 1e-6",
+    pore = mask == 0
+    sync = torch.cuda.synchronize
+    out = {"criterion": "k within 0.1% of the FP64 k_inf for 10 consecutive checks (every 100 steps)",
            "step_variant": "%d: %s" % (variant, VARIANT_NAMES[variant])}
     with Lattice(mask, TAU, "mrt", "fp32", stream=stream) as lat:
         lat.set_kernel(variant)
         lat.set_flux_bc(Q)
-        r = cv.run_to_residual(lat, Q, TAU, lag=1000, tol=1e-6, max_steps=max_steps,
-                               sync=torch.cuda.synchronize)
-    k_inf = r["k"]
+        r32 = cv.run_to_residual(lat, Q, TAU, lag=1000, tol=1e-6, max_steps=max_steps, sync=sync)
+        f32 = lat.distributions()
+    out["fp32_reference_run"] = {"steps": r32["steps"], "seconds": round(r32["seconds"], 3),
+                                 "residual": r32["residual"], "converged": r32["converged"], "k": r32["k"]}
+    with Lattice(mask, TAU, "mrt", "fp64", stream=stream) as lat:
+        lat.set_kernel(variant)
+        lat.set_flux_bc(Q)
+        lat.set_distributions(f32)
+        r64 = cv.run_to_residual(lat, Q, TAU, lag=1000, tol=1e-6, max_steps=40000, sync=sync, min_steps=6000)
+        f64 = lat.fields()
+    del f32
+    k_inf, q64 = r64["k"], r64["q_out"]
+    u64 = f64[1:]
     out["k_inf"] = k_inf
-    out["k_inf_run"] = {"steps": r["steps"], "seconds": round(r["seconds"], 3), "residual": r["residual"],
-                        "converged": r["converged"], "q_out_rel_err": abs(r["q_out"] - Q) / Q}
+    out["fp64_reference_run"] = {"start": "the FP32 steady state's distributions", "steps": r64["steps"],
+                                 "seconds": round(r64["seconds"], 3), "residual": r64["residual"],
+                                 "converged": r64["converged"], "k": k_inf, "q_out_rel_to_Q": (q64 - Q) / Q,
+                                 "fp32_reference_k_rel": (r32["k"] - k_inf) / k_inf}
     for prec in precs:
         with Lattice(mask, TAU, "mrt", prec, stream=stream) as lat:
             lat.set_kernel(variant)
             lat.set_flux_bc(Q)
-            rr = cv.run_to_reference(lat, Q, TAU, k_inf, max_steps=min(max_steps, 60000),
-                                     sync=torch.cuda.synchronize)
+            rr = cv.run_to_reference(lat, Q, TAU, k_inf, max_steps=min(max_steps, 60000), sync=sync)
+            at_rule = error_block(lat, Q, k_inf, q64, u64, pore)
+        with Lattice(mask, TAU, "mrt", prec, stream=stream) as lat:
+            lat.set_kernel(variant)
+            lat.set_flux_bc(Q)
+            lat.set_fields(*f64)
+            lat.step(bias_steps)
+            steady = error_block(lat, Q, k_inf, q64, u64, pore)
         out[prec] = {"steps": rr["steps"], "seconds": None if rr["seconds"] is None else round(rr["seconds"], 3),
-                     "reached": rr["reached"], "k_rel_err_at_end": (rr["k"] - k_inf) / k_inf,
-                     "q_out_rel_err_at_end": (rr["q_out"] - Q) / Q, "steps_run": rr["steps_run"]}
+                     "reached": rr["reached"], "steps_run": rr["steps_run"],
+                     "vs_fp64": {"at_rule": at_rule,
+                                 "steady": dict(steady, note="from the FP64 steady state, %d steps" % bias_steps)}}
     return out
 
 
@@ -472,9 +603,11 @@ def run_two_fluid(stream, steps=500, warmup=20, total_steps=50000):
         c.step(total_steps - warmup - steps)
         q_in_end, rho_in_end = c.get_flux(4)
     n = int((mask == 0).sum())
-    unit = 82 * 4  # FP32 values per node and step: f 19+19, A/B 14+14, phase 1, pre-pass A/B 14 + phi 1
+    unit = 82 * 4  # FP32 values per node and step as built: f 19+19, A/B 14+14, phase 1, pre-pass A/B 14 + phi 1
+    unit_min = 66 * 4  # a single pass: f 19+19, A/B 14+14
     peak, _ = measured_hbm_peak()
     ach = unit * n / (ms * 1e-3 / steps) / 1e9
+    ach_min = unit_min * n / (ms * 1e-3 / steps) / 1e9
     return {"workload": "two-fluid colour model, 192x192x384 sphere pack (radii 5-10, porosity %.3f, 6+6 "
                         "reservoir layers, inlet reservoir non-wetting), tau 1, alpha %g, beta %g, wetting solid, non-wetting injected "
                         "at Ca 1e-5, FP32" % (eps, alpha, beta),
@@ -482,10 +615,30 @@ def run_two_fluid(stream, steps=500, warmup=20, total_steps=50000):
             "MLUPS": round(n * steps / (ms * 1e-3) / 1e6, 1), "ms_per_step": round(ms / steps, 5),
             "roofline": {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(ach / peak, 4), "bytes_per_unit": unit,
-                         "kernels": "k_color_pre + k_color_step"},
+                         "kernels": "k_color_pre + k_color_step",
+                         "single_pass": {"bytes_per_unit": unit_min, "achieved": round(ach_min, 1),
+                                         "frac": round(ach_min / peak, 4),
+                                         "note": "against the 66 values a single-pass step must move; the "
+                                                 "pre-pass re-reads the 14 D3Q7 values and writes and reads phi"}},
             "inlet_flux_rel_err": abs(q_in - Q) / Q,
             "run_to_step": total_steps,
             "inlet_flux_rel_err_end": abs(q_in_end - Q) / Q, "rho_in_end": rho_in_end}
+
+
+def cpu_baseline(mask, seconds_per_step, steps):
+    """The FP64 oracle as it stands on every host core: one single-threaded
+    child per core, each on its own slab of the pack, all at once."""
+    cores = host_cores()
+    probe_mlups, _, _ = oracle_rate(mask[:16].copy(), 1)
+    samples = oracle_samples(mask, seconds_per_step, probe_mlups, cores)
+    r = oracle_rate_parallel(samples, steps)
+    shp = samples[0].shape
+    return {"value": round(r["mlups"], 4), "unit": METRIC, "cores": r["children"], "kind": "oracle",
+            "cpu_model": host_cpu_model(), "single_core_probe_mlups": round(probe_mlups, 4),
+            "sample": "FP64 numpy oracle, %d single-threaded processes at once (one per host core), %d steps "
+                      "each on its own %dx%dx%d z-slab of the same pack (slabs spread over the depth; %d pore "
+                      "nodes in all; %.1f s)" % (r["children"], steps, shp[2], shp[1], shp[0], r["n_pore"],
+                                                 r["seconds"])}
 
 
 # ------------------------------------------------------------- our path ---
@@ -583,15 +736,14 @@ def run_ours(args, rank, world, local):
     if rank == 0 and args.steady:
         steady = time_to_steady(mask, a_in, stream, variant=args.variant)
 
+    warm = None
+    if rank == 0 and args.ws_leg:
+        warm = run_warmstart_leg(stream, args.ws_samples, 64, args.ws_lbm_steps, args.ws_epochs, 256,
+                                 args.variant, args.ws_ref_steps)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        probe_mlups, _, _ = oracle_rate(mask[:16].copy(), 1)
-        sample = crop_for_budget(mask, 8.0, probe_mlups)
-        c_mlups, c_sec, c_n = oracle_rate(sample, 2)
-        cpu = {"value": round(c_mlups, 4), "unit": METRIC, "cores": 1, "kind": "oracle",
-               "sample": "FP64 numpy oracle, single thread, 2 steps on the inlet-side %dx%dx%d slab of "
-                         "the same pack (%d pore nodes, %.1f s)" % (sample.shape[2], sample.shape[1],
-                                                                      sample.shape[0], c_n, c_sec)}
+        cpu = cpu_baseline(mask, seconds_per_step=3.0, steps=3)
 
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": METRIC, "n_gpus": world, "steps": K,
@@ -609,6 +761,8 @@ def run_ours(args, rank, world, local):
                    "device": dev_name},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": traffic,
+                     "frac_vs_nominal": round(achieved / NOMINAL_HBM_GBS, 4),
+                     "nominal_peak": NOMINAL_HBM_GBS,
                      "kernel": "k_step_aa<odd/even> (alternating; each launch is one full step; "
                                "pair mean)" if variant == 3 else "k_step",
                      "kernel_ms": round(ms_step_k, 5), "per_kernel": per_kernel,
@@ -621,6 +775,7 @@ def run_ours(args, rank, world, local):
         "gpu_launches": K + (2 * (K // 1024) if prec in ("fp16dev", "bf16dev") else 0)
                         + ((2 + (K & 1)) if variant == 3 else 0),
         "time_to_steady": steady,
+        "warm_start": warm,
         "ensemble": ens,
         "two_fluid": two,
         "clocks": clk,
@@ -638,81 +793,174 @@ def run_reference(args, rank, world, local):
         return
     mask, info, a_in = workload()
     K, W = args.steps, args.warmup
-    probe_mlups, _, _ = oracle_rate(mask[:16].copy(), 1)
     per_step = max(0.02, min(8.0, 60.0 / max(1, K + W)))
-    sample = crop_for_budget(mask, per_step, probe_mlups)
+    cores = host_cores()
+    probe_mlups, _, _ = oracle_rate(mask[:16].copy(), 1)
+    samples = oracle_samples(mask, per_step, probe_mlups, cores)
     if W:
-        oracle_rate(sample, W)
-    mlups, sec, n_s = oracle_rate(sample, K)
-    desc = ("FP64 numpy oracle, single thread; each step is one oracle step on the inlet-side "
-            "%dx%dx%d sample of the 256^3 pack (%d pore nodes)" % (sample.shape[2], sample.shape[1],
-                                                                   sample.shape[0], n_s))
-    line = {"impl": "reference", "metric": METRIC, "value": round(mlups, 4), "unit": METRIC,
-            "n_gpus": world, "steps": K, "warmup": W, "ms_per_step": round(1e3 * sec / K, 3),
+        oracle_rate_parallel(samples, W)
+    r = oracle_rate_parallel(samples, K)
+    shp = samples[0].shape
+    desc = ("FP64 numpy oracle, %d single-threaded processes at once (one per host core); each step is one "
+            "oracle step of every process on its own %dx%dx%d z-slab of the 256^3 pack (%d pore nodes in all)"
+            % (r["children"], shp[2], shp[1], shp[0], r["n_pore"]))
+    line = {"impl": "reference", "metric": METRIC, "value": round(r["mlups"], 4), "unit": METRIC,
+            "n_gpus": world, "steps": K, "warmup": W, "ms_per_step": round(1e3 * r["seconds"] / K, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": "D3Q19 MRT flux-BC LBM, 256^3 sphere pack (radii 6-12, porosity %.3f, "
                                    "6+6 reservoir layers), tau 0.7, u_mean 1e-4" % info["porosity"],
                        "sample": desc},
-            "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": desc, "value": round(mlups, 4),
-                             "unit": METRIC},
-            "e2e": {"value": round(mlups, 4), "unit": METRIC, "h2d_bytes_per_step": 0,
+            "cpu_baseline": {"kind": "oracle", "cores": r["children"], "cpu_model": host_cpu_model(),
+                             "sample": desc, "value": round(r["mlups"], 4), "unit": METRIC},
+            "e2e": {"value": round(r["mlups"], 4), "unit": METRIC, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def run_warmstart(args):
-    """Learned warm start experiment: train the network on LBM steady states of
-    seeded 64^3 sphere packs (radii U[8,16], porosity U[0.25,0.45]) computed by
-    this library, then compare steps and wall time to the 0.1 % steady rule
-    from a cold and from a warm start on a larger seeded pack."""
+def net_flops(levels=4, base=32, side=64):
+    """Algorithmic FLOPs of one sample's forward pass (2 per multiply-add, real
+    channels, interior voxels) and of a training step's forward + backward (data
+    gradients of every layer but the first, weight gradients of all)."""
+    c = [base << l for l in range(levels)]
+    lay = [(c[0], 1, 0), (c[0], c[0], 0)]
+    for l in range(1, levels):
+        lay += [(c[l], c[l - 1], l), (c[l], c[l], l)]
+    for l in range(levels - 2, -1, -1):
+        lay += [(c[l], c[l + 1], l), (c[l], c[l], l)]
+    lay.append((3, c[0], 0))
+    f = [2.0 * 27 * co * ci * (side >> l) ** 3 for co, ci, l in lay]
+    return sum(f), 3 * sum(f) - f[0]
+
+
+def conv_roofline(stream, side=64, batch=8, reps=20):
+    """CUDA-event times of the dominant convolution shape of the network (32 ->
+    32 channels at full resolution, 8 samples of 64^3: 2.1 M voxels) for the
+    forward, data-gradient and weight-gradient kernels, as tensor-core
+    throughput on interior voxels against the measured BF16 dense peak."""
+    import torch
+
+    from paper_1806_10589_gb300 import conv3d_bf16
+
+    g = torch.Generator(device="cuda").manual_seed(3)
+    shp = (batch, side + 2, side + 2, side + 2, 32)
+    a = torch.zeros(shp, dtype=torch.bfloat16, device="cuda")
+    gr = torch.zeros(shp, dtype=torch.bfloat16, device="cuda")
+    a[:, 1:-1, 1:-1, 1:-1] = torch.randn((batch, side, side, side, 32), generator=g, device="cuda").bfloat16()
+    gr[:, 1:-1, 1:-1, 1:-1] = torch.randn((batch, side, side, side, 32), generator=g, device="cuda").bfloat16()
+    w = (torch.randn((32, 27, 32), generator=g, device="cuda") * 0.03).bfloat16()
+    out = torch.empty(shp, dtype=torch.bfloat16, device="cuda")
+    gw = torch.zeros((32, 27, 32), dtype=torch.float32, device="cuda")
+    args = (batch, side, side, side, 32, 32)
+    conv3d_bf16(0, a.data_ptr(), 0, w.data_ptr(), 0, 1, out.data_ptr(), *args, stream=stream)  # warm-up
+    ms = {"forward": conv3d_bf16(0, a.data_ptr(), 0, w.data_ptr(), 0, 1, out.data_ptr(), *args, stream=stream,
+                                 reps=reps),
+          "data_gradient": conv3d_bf16(1, gr.data_ptr(), 0, w.data_ptr(), 0, 0, out.data_ptr(), *args,
+                                       stream=stream, reps=reps),
+          "weight_gradient": conv3d_bf16(2, a.data_ptr(), gr.data_ptr(), w.data_ptr(), 0, 0, gw.data_ptr(), *args,
+                                         stream=stream, reps=reps)}
+    flops = 2.0 * 27 * 32 * 32 * batch * side ** 3
+    peak, kind = measured_bf16_peak()
+    per = {k: {"ms": round(v, 5), "achieved": round(flops / (v * 1e-3) / 1e12, 1),
+               "frac": round(flops / (v * 1e-3) / 1e12 / peak, 4)} for k, v in ms.items()}
+    top = min(ms, key=ms.get)
+    return {"bound": "tensor", "unit": "TFLOP/s", "peak": peak, "peak_source": kind,
+            "shape": "3x3x3 conv 32 -> 32 channels, %d x %d^3 voxels (BF16, FP32 accumulate)" % (batch, side),
+            "flops_per_launch": flops, "per_kernel": per, "achieved": per[top]["achieved"],
+            "frac": per[top]["frac"], "kernel": "k_conv<32,32> / k_wgrad<32,32>", "traffic": None}
+
+
+def run_warmstart_leg(stream, samples=512, side=64, lbm_steps=8000, epochs=30, test_side=256, variant=3,
+                      ref_steps=300000):
+    """Learned warm start: train the network (4 levels, 32 base channels) on LBM
+    steady states of seeded 64^3 sphere packs (radii U[8,16], porosity
+    U[0.25,0.45]) computed by this library, then run five starts of a seeded
+    test pack (radii 8-16, porosity 0.35) to the 0.1 % rule: cold, the
+    Kozeny-Carman density ramp (no network), the network's velocity only, its
+    pressure only, and both.  Clocks are sampled over the whole leg."""
     import torch
 
     from paper_1806_10589_gb300 import Batch, Lattice, WarmStartNet, convergence as cv, warmstart as ws
 
-    torch.cuda.set_device(0)
-    stream = torch.cuda.current_stream()
+    sync = torch.cuda.synchronize
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
     rng = np.random.default_rng(11)
-    S, side = args.ws_samples, 64
     t0 = time.perf_counter()
-    masks = [sphere_pack(side, 8.0, 16.0, float(rng.uniform(0.25, 0.45)), seed=5000 + k)[0] for k in range(S)]
+    masks = [sphere_pack(side, 8.0, 16.0, float(rng.uniform(0.25, 0.45)), seed=5000 + k)[0] for k in range(samples)]
     t_geo = time.perf_counter() - t0
     t0 = time.perf_counter()
-    targets, ks = ws.steady_targets(Batch, masks, TAU, UBAR, args.ws_lbm_steps, stream=stream)
-    torch.cuda.synchronize()
+    targets, ks = ws.steady_targets(Batch, masks, TAU, UBAR, lbm_steps, stream=stream)
+    sync()
     t_lbm = time.perf_counter() - t0
     c_kc = ws.fit_kc(masks, ks)
     net = WarmStartNet(4, 32, stream=stream)
     net.set_params(ws.he_init(net, seed=4))
-    ntr = int(0.9 * S)
+    ntr = int(0.9 * samples)
+    sync()
     t0 = time.perf_counter()
-    hist = net.train(np.stack(masks[:ntr]), targets[:ntr], epochs=args.ws_epochs, batch=8, lr=1e-3, seed=1)
+    hist = net.train(np.stack(masks[:ntr]), targets[:ntr], epochs=epochs, batch=8, lr=1e-3, seed=1)
     t_train = time.perf_counter() - t0
     val_loss = float(np.mean([net.loss_grad(np.stack(masks[j:j + 1]), targets[j:j + 1])[0]
-                              for j in range(ntr, S)]))
-    test_mask, _ = sphere_pack(args.ws_test, 8.0, 16.0, 0.35, seed=777)
-    A = int((test_mask[0] == 0).sum())
-    Q = UBAR * A
+                              for j in range(ntr, samples)]))
+    _, f_step = net_flops(4, 32, side)
+    train_flops = f_step * ntr * epochs
+    test_mask, _ = sphere_pack(test_side, 8.0, 16.0, 0.35, seed=777)
+    Q = UBAR * int((test_mask[0] == 0).sum())
     t0 = time.perf_counter()
     with Lattice(test_mask, TAU, "mrt", "fp32", stream=stream) as lat:
-        lat.set_kernel(args.variant)
+        lat.set_kernel(variant)
         lat.set_flux_bc(Q)
         n_test = lat.info()["n_pore"]
-        ref = cv.run_to_residual(lat, Q, TAU, lag=1000, tol=1e-6, max_steps=args.ws_ref_steps,
-                                 sync=torch.cuda.synchronize)
+        ref = cv.run_to_residual(lat, Q, TAU, lag=1000, tol=1e-6, max_steps=ref_steps, sync=sync)
     t_ref = time.perf_counter() - t0
-    res = ws.warm_vs_cold(Lattice, net, test_mask, Q, TAU, c_kc, ref["k"], stream=stream,
-                          sync=torch.cuda.synchronize, max_steps=args.ws_ref_steps, variant=args.variant)
-    out = {"warmstart": {
-        "train": {"samples": S, "side": side, "lbm_steps": args.ws_lbm_steps, "epochs": args.ws_epochs,
-                  "loss_first": float(hist[0]), "loss_last": float(hist[-1]), "val_loss": val_loss,
-                  "c_kc": c_kc, "seconds": {"geometry": round(t_geo, 1), "lbm": round(t_lbm, 1),
-                                            "train": round(t_train, 1)}},
-        "test": {"side": args.ws_test, "n_pore": n_test, "step_variant": args.variant,
-                 "k_ref": ref["k"], "k_ref_steps": ref["steps"], "k_ref_seconds": round(t_ref, 1),
-                 "k_ref_converged": ref["converged"], **res}}}
-    print(json.dumps(out), flush=True)
+    abl = ws.ablation(Lattice, net, test_mask, Q, TAU, c_kc, ref["k"], stream=stream, sync=sync,
+                      max_steps=ref_steps, variant=variant)
+    k_net = ws.net_permeability(net, test_mask, Q, TAU)
+    k_kc = c_kc * ws.kc_features(test_mask)[2]
+    clk = clocks.stop()
+    conv = conv_roofline(stream)
     net.close()
+
+    def change(name, base):
+        a, b = abl[name], abl[base]
+        if not (a["reached"] and b["reached"]):
+            return None
+        return {"steps": round(a["steps"] / b["steps"] - 1.0, 4), "seconds": round(a["seconds"] / b["seconds"] - 1.0, 4)}
+
+    return {"train": {"network": "U-Net, 4 levels, 32/64/128/256 channels, 15 3x3x3 convolutions, BF16 weights "
+                                 "and activations, FP32 accumulate (tcgen05)",
+                      "samples": samples, "train_samples": ntr, "side": side, "lbm_steps": lbm_steps,
+                      "epochs": epochs, "batch": 8, "loss_first": float(hist[0]), "loss_last": float(hist[-1]),
+                      "val_loss": val_loss, "c_kc": c_kc,
+                      "seconds": {"geometry": round(t_geo, 1), "lbm": round(t_lbm, 1), "train": round(t_train, 2)},
+                      "train_tflops_algorithmic": round(train_flops / t_train / 1e12, 1)},
+            "test": {"side": test_side, "n_pore": n_test, "step_variant": variant, "k_ref": ref["k"],
+                     "k_ref_steps": ref["steps"], "k_ref_seconds": round(t_ref, 1), "k_ref_converged": ref["converged"],
+                     "criterion": "k within 0.1% of k_ref for 10 consecutive checks (every 100 steps); the time "
+                                  "of a warm start includes inference and upload",
+                     "starts": abl,
+                     "starts_defined": {"cold": "rho 1, u 0", "kc_ramp": "rho: Kozeny-Carman Darcy ramp, u 0 (no "
+                                        "network)", "net_velocity": "u: network, rho 1",
+                                        "net_pressure": "rho: network pressure profile, u 0",
+                                        "net": "u and rho from the network"},
+                     "change_vs_cold": {n: change(n, "cold") for n in ("kc_ramp", "net_velocity", "net_pressure",
+                                                                       "net")},
+                     "net_vs_kc_ramp": change("net", "kc_ramp"),
+                     "permeability_estimates": {"k_ref": ref["k"], "kozeny_carman": k_kc,
+                                                "kozeny_carman_rel_err": (k_kc - ref["k"]) / ref["k"],
+                                                "network": k_net, "network_rel_err": (k_net - ref["k"]) / ref["k"]}},
+            "conv_roofline": conv, "clocks": clk}
+
+
+def run_warmstart(args):
+    """The learned warm-start leg alone (e.g. on a 512^3 test pack)."""
+    import torch
+
+    torch.cuda.set_device(0)
+    out = {"warmstart": run_warmstart_leg(torch.cuda.current_stream(), args.ws_samples, 64, args.ws_lbm_steps,
+                                          args.ws_epochs, args.ws_test, args.variant, args.ws_ref_steps)}
+    print(json.dumps(out), flush=True)
 
 
 def run_profile_case(args):
@@ -725,6 +973,24 @@ def run_profile_case(args):
     from paper_1806_10589_gb300 import ColorLattice, Lattice, drainage
 
     torch.cuda.set_device(0)
+    if args.conv_case:
+        r = conv_roofline(torch.cuda.current_stream(), reps=max(1, args.steps))
+        print(json.dumps({"profile_case": "conv", "per_kernel": r["per_kernel"]}))
+        return
+    if args.ensemble_case:
+        from paper_1806_10589_gb300 import Batch
+
+        masks, Qs, _ = ensemble_workload()
+        with Batch(masks, TAU, "mrt", "fp16dev", stream=torch.cuda.current_stream()) as b:
+            b.set_config(1)  # per-step launches, 48-register cap (the autotuner's usual pick)
+            for k, q in enumerate(Qs):
+                b.set_flux_bc(k, q)
+            for _ in range(args.warmup):
+                b.step(1)
+            ms = b.time_step(args.steps)
+            n = b.info()["n_pore"]
+        print(json.dumps({"profile_case": "ensemble fp16dev", "n_pore": n, "step_ms": ms}))
+        return
     if args.two_fluid_case:
         mask, info = sphere_pack((192, 192, 384), 5.0, 10.0, 0.35, seed=31, reservoir=6)
         nz, ny, nx = mask.shape
@@ -765,8 +1031,10 @@ def main(argv=None):
                     help="also time the batched 64-member ensemble (FP16 deviation storage)")
     ap.add_argument("--two-fluid", action=argparse.BooleanOptionalAction, default=True,
                     help="also time the two-fluid colour model on a 192x192x384 pack")
+    ap.add_argument("--ws-leg", action=argparse.BooleanOptionalAction, default=True,
+                    help="also train the warm-start network and run its four-start ablation on a 256^3 pack")
     ap.add_argument("--warmstart", action="store_true",
-                    help="run the learned warm-start experiment instead of the benchmark")
+                    help="run the learned warm-start leg alone instead of the benchmark (see --ws-test)")
     ap.add_argument("--ws-samples", type=int, default=512)
     ap.add_argument("--ws-lbm-steps", type=int, default=8000)
     ap.add_argument("--ws-epochs", type=int, default=30)
@@ -774,6 +1042,11 @@ def main(argv=None):
     ap.add_argument("--ws-ref-steps", type=int, default=300000)
     ap.add_argument("--two-fluid-case", action="store_true",
                     help="with --profile-case: the two-fluid pack instead of the benchmark lattice")
+    ap.add_argument("--conv-case", action="store_true",
+                    help="with --profile-case: the network's 32 -> 32 convolution kernels (forward, data and "
+                         "weight gradient), --steps launches each")
+    ap.add_argument("--ensemble-case", action="store_true",
+                    help="with --profile-case: the 64-member FP16-dev ensemble, per-step launches")
     ap.add_argument("--profile-case", action="store_true",
                     help="run the short fixed launch sequence used for ncu captures")
     args = ap.parse_args(argv)

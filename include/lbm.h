@@ -324,14 +324,16 @@ const char* lbm_color_last_error(const lbm_color* c);
  * specified network: levels = 4, base = 32, i.e. 32/64/128/256 channels, 15
  * convolutions; every channel count must be 32, 64, 128 or 256), 3x3x3
  * convolutions, ReLU, 2x2x2 mean pooling, nearest upsampling and additive
- * skips, maps a voxel geometry to the steady velocity field divided by the
- * superficial velocity u_D = Q / (nx ny).  The convolutions (forward, data
+ * skips, maps a voxel geometry to 4 steady-state fields: the velocity divided
+ * by the superficial velocity u_D = Q / (nx ny), and the pressure gradient
+ * G = -(p(z+1) - p(z)) / (nu u_D), p = rho / 3, nu = (tau - 1/2) / 3.  The convolutions (forward, data
  * gradient, weight gradient) run on the tcgen05 tensor cores with BF16
  * weights and activations and FP32 accumulation; pooling, upsampling, loss
  * and Adam run in this library's CUDA kernels; the master parameters and Adam
  * state are FP32.  All volumes have sides divisible by 2^(levels-1); masks are
  * uint8 [z][y][x], 1 = solid (as for lbm_create); fields are float32
- * [c][z][y][x] with c = u_x, u_y, u_z.  Parameters are stored layer by layer
+ * [c][z][y][x] with c = u_x, u_y, u_z, G; a NaN target entry has no target
+ * (it adds nothing to the loss).  Parameters are stored layer by layer
  * (forward order) as W[cout][27][cin] (taps dz, dy, dx each in -1, 0, 1, then
  * the input channel) followed by b[cout]; they start at 0 until set.  A
  * tensor-core pipeline wait that runs out (bounded at about one second)
@@ -344,7 +346,8 @@ int lbm_wsnet_set_stream(lbm_wsnet* net, void* cuda_stream);
 int lbm_wsnet_set_params(lbm_wsnet* net, const float* params);   /* host, num_params floats; resets Adam */
 int lbm_wsnet_get_params(lbm_wsnet* net, float* params);         /* host, num_params floats */
 /* Masked mean squared error over pore voxels of `batch` samples (host arrays:
- * masks batch*nz*ny*nx bytes, targets batch*3*nz*ny*nx floats) and its gradient
+ * masks batch*nz*ny*nx bytes, targets batch*4*nz*ny*nx floats; divided by
+ * 4 * the pore count) and its gradient
  * w.r.t. the parameters (host, num_params floats; may be NULL). */
 int lbm_wsnet_loss_grad(lbm_wsnet* net, const uint8_t* masks, const float* targets, int batch, int nx, int ny,
                         int nz, double* loss, float* grad);
@@ -354,7 +357,7 @@ int lbm_wsnet_loss_grad(lbm_wsnet* net, const uint8_t* masks, const float* targe
  * (epochs floats, may be NULL).  Synchronises. */
 int lbm_wsnet_train(lbm_wsnet* net, const uint8_t* masks, const float* targets, int n_samples, int nx, int ny,
                     int nz, int epochs, int batch, float lr, const int* order, float* loss_history);
-/* Predicted u / u_D (host, 3*nz*ny*nx floats) of one geometry; 0 at solids. */
+/* Predicted fields (host, 4*nz*ny*nx floats) of one geometry; 0 at solids. */
 int lbm_wsnet_predict(lbm_wsnet* net, const uint8_t* mask, int nx, int ny, int nz, float* y);
 /* Free the activation buffers kept between calls (sized for the last batch and volume). */
 int lbm_wsnet_release_buffers(lbm_wsnet* net);
@@ -380,6 +383,12 @@ const char* lbm_wsnet_last_error(const lbm_wsnet* net);
  * LBM_ETIMEOUT if a pipeline wait ran out. */
 int lbm_conv3d_bf16(int op, const void* in, const void* aux, const void* w, const float* bias, int relu, void* out,
                     int batch, int nx, int ny, int nz, int cin, int cout, void* cuda_stream);
+/* The same convolution launched `reps` times back to back on `cuda_stream`,
+ * bracketed by CUDA events on that stream; *ms_per_call = the mean time of
+ * one launch.  For op 2 the weight gradient is added `reps` times. */
+int lbm_conv3d_bf16_time(int op, const void* in, const void* aux, const void* w, const float* bias, int relu,
+                         void* out, int batch, int nx, int ny, int nz, int cin, int cout, int reps,
+                         float* ms_per_call, void* cuda_stream);
 
 #ifdef __cplusplus
 }

@@ -13,8 +13,10 @@ Network (c_l = base * 2^l channels at level l; every side divisible by
     El a = relu(conv(pool(E(l-1)b))), El b = relu(conv(El a))     l = 1 .. L-1
     Dl a = relu(conv(up(D(l+1)b)))  (D(L-1)b := E(L-1)b)          l = L-2 .. 0
     Sl   = Dl a + El b,      Dl b = relu(conv(Sl))
-    Y    = conv(D0b) * X                                          3 channels (u / u_D)
-    loss = sum over pore voxels and channels of (Y - T)^2 / (3 n_pore)
+    Y    = conv(D0b) * X         4 channels: u / u_D (3) and G = -dp/dz / (nu u_D)
+    loss = sum over the entries with a target of (Y - T)^2 / (4 n_pore)
+A target entry that is NaN has no target (the G channel is defined only where
+a pore voxel's +z neighbour is a pore too); it adds nothing to the loss.
 conv: 3x3x3 cross-correlation with zero padding and a bias; pool: 2x2x2 mean;
 up: nearest-neighbour 2x.  Parameters are stored layer by layer (in the order
 the convolutions run above) as W[co][27][ci] -- the 27 taps ordered dz, dy, dx,
@@ -25,6 +27,7 @@ from __future__ import annotations
 import numpy as np
 
 TAPS = [(dz, dy, dx) for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1)]
+NOUT = 4  # output channels: u_x, u_y, u_z (over u_D) and the pressure gradient G
 
 
 def channels(levels=4, base=32):
@@ -39,7 +42,7 @@ def layer_shapes(levels=4, base=32):
         shapes += [(c[l], c[l - 1]), (c[l], c[l])]
     for l in range(levels - 2, -1, -1):
         shapes += [(c[l], c[l + 1]), (c[l], c[l])]
-    shapes.append((3, c[0]))
+    shapes.append((NOUT, c[0]))
     return shapes
 
 
@@ -156,9 +159,11 @@ def loss_and_grad(params, pore, target, levels=4, base=32):
     Y, A = forward(params, pore, levels, base, keep=True)
     X = A["X"]
     npore = X.sum()
-    diff = (Y - target) * X
-    loss = (diff ** 2).sum() / (3.0 * npore)
-    gY = 2.0 * diff / (3.0 * npore)
+    target = np.asarray(target, dtype=np.float64)
+    has = ~np.isnan(target)
+    diff = np.where(has, Y - np.where(has, target, 0.0), 0.0) * X
+    loss = (diff ** 2).sum() / (NOUT * npore)
+    gY = 2.0 * diff / (NOUT * npore)
     nl = len(Ls)
     grads = [None] * nl
 

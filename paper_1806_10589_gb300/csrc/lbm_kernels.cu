@@ -470,6 +470,11 @@ struct AAPtrs {
 #ifndef LBM_AA_PREFETCH
 #define LBM_AA_PREFETCH 224
 #endif
+// LBM_AA16_PREFETCH: the same bulk L2 prefetch for the 16-bit gather-scatter
+// step, that many blocks ahead; 0 = off.
+#ifndef LBM_AA16_PREFETCH
+#define LBM_AA16_PREFETCH 0
+#endif
 template <class S, bool ODD>
 constexpr int aa_min_blocks() {
     if constexpr (sizeof(typename S::M) == 8) return 1;
@@ -505,10 +510,12 @@ k_step_aa(const AAPtrs<typename S::T> F, int slot, DevLattice L, typename S::M s
     const int64_t i64 = (int64_t)blockIdx.x * kBlock + threadIdx.x;
     const int i = (int)i64;
     double part = 0.0;
-    if constexpr (ODD && !S::kRef && LBM_AA_PREFETCH > 0) {
+    constexpr int kAhead = S::kRef ? LBM_AA16_PREFETCH : LBM_AA_PREFETCH;
+    if constexpr (ODD && kAhead > 0) {
         // threads 0..18: row q of the buffer (rows are F.row[0] + q ns, as
-        // launched); thread 19: the voxel list, cut to a multiple of 4 entries
-        const int64_t s = ((int64_t)blockIdx.x + LBM_AA_PREFETCH) * kBlock;
+        // launched; 128-element padding keeps every range 16-byte aligned for
+        // 2-byte values too); thread 19: the voxel list, cut to a multiple of 4 entries
+        const int64_t s = ((int64_t)blockIdx.x + kAhead) * kBlock;
         const int t = (int)threadIdx.x;
         if (t < 19) l2_prefetch_range(F.row[0] + (int64_t)t * L.ns, s, kBlock, L.ns);
         else if (t == 19) l2_prefetch_range(L.vox, s, kBlock, L.n & ~(int64_t)3);

@@ -10,15 +10,17 @@
 //   Ela = relu(conv(pool(E(l-1)b))), Elb = relu(conv(Ela))           l = 1 .. L-1
 //   Dla = relu(conv(up(D(l+1)b))), Sl = Dla + Elb,                   l = L-2 .. 0
 //   Dlb = relu(conv(Sl))                        (D(L-1)b = E(L-1)b)
-//   Y   = conv(D0b) * X          (3 channels; X = pore indicator)
+//   Y   = conv(D0b) * X          (4 channels: u / u_D and G = -dp/dz / (nu u_D);
+//                                 X = pore indicator)
 // conv = 3x3x3 cross-correlation, zero padding, bias; pool = 2x2x2 mean;
-// up = nearest 2x.  Loss = masked mean squared error over pore voxels.
+// up = nearest 2x.  Loss = masked mean squared error over the entries that
+// have a target (a NaN target entry has none).
 // Parameters (FP32 master copy, Adam state) per layer: W[co][27][ci] (taps dz,
 // dy, dx in -1..1, then the input channel) then b[co].
 //
 // Activation layout: BF16, channels last, with a one-voxel zero border:
 // [B][Z+2][Y+2][X+2][C], C in {32, 64, 128, 256} (the 1-channel input and the
-// 3-channel output are zero-padded to 32 channels).  In this layout a 3x3x3
+// 4-channel output are zero-padded to 32 channels).  In this layout a 3x3x3
 // tap is a constant row offset, so the implicit-GEMM operand of tap t for the
 // 128 output rows r0 .. r0+127 is the contiguous row range r0 + off(t): one
 // TMA box.  Outputs on border rows are computed and discarded (written 0).
@@ -56,6 +58,7 @@ namespace {
 
 constexpr int kThreads = 192;  // warp 0: TMA, warp 1: MMA + TMEM, warps 2-5: epilogue
 constexpr int kRows = 128;     // output rows per tile (MMA M)
+constexpr int kOut = 4;        // network output channels: u / u_D (3), pressure gradient G
 
 __host__ __device__ constexpr int cmin(int a, int b) { return a < b ? a : b; }
 __host__ __device__ constexpr int pow2_at_least(int v) {
@@ -136,7 +139,7 @@ struct ConvEpi {
     bf16* out_add;
     const bf16* mask;           // out_mask = v * (mask > 0)
     bf16* out_mask;
-    float* y;                   // output layer: y[b][c][z][y][x] = v * pore, c < 3
+    float* y;                   // output layer: y[b][c][z][y][x] = v * pore, c < kOut
     const bf16* xin;            // pore indicator rows (channel 0 of a 32-channel tensor)
     int* err;
     PGeo g;
@@ -252,7 +255,7 @@ k_conv(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorM
                 const int64_t n = (int64_t)e.g.Z * e.g.Y * e.g.X;
                 const int64_t o3 = ((int64_t)z * e.g.Y + y) * e.g.X + x;
 #pragma unroll
-                for (int c = 0; c < 3; ++c) e.y[((int64_t)b * 3 + c) * n + o3] = v[c] * pore;
+                for (int c = 0; c < kOut; ++c) e.y[((int64_t)b * kOut + c) * n + o3] = v[c] * pore;
             }
         }
     }
@@ -517,7 +520,8 @@ __global__ void k_pool_bwd_add_mask(const bf16* __restrict__ gcoarse, const bf16
     }
 }
 
-// masked MSE over interior voxels: gz[row] = (2 inv (Y - T) pore for c < 3, 0 else), loss += inv sum (Y - T)^2 pore
+// masked MSE over interior voxels: gz[row] = (2 inv (Y - T) pore for c < kOut with a target, 0 else),
+// loss += inv sum (Y - T)^2 pore; a NaN target entry has no target
 __global__ void k_mse(const float* __restrict__ Y, const float* __restrict__ T, const bf16* __restrict__ x32,
                       bf16* __restrict__ gz, PGeo g, double inv, double* loss) {
     __shared__ double sh[32];
@@ -531,15 +535,16 @@ __global__ void k_mse(const float* __restrict__ Y, const float* __restrict__ T, 
         const int64_t r = g.row(b, z, y, x);
         const float pore = __bfloat162float(x32[r * 32]) > 0.f ? 1.f : 0.f;
         float f[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        const int64_t o = (int64_t)b * 3 * N + k - (int64_t)b * N;
-        for (int c = 0; c < 3; ++c) {
-            const float d = (Y[o + c * N] - T[o + c * N]) * pore;
+        const int64_t o = (int64_t)b * kOut * N + k - (int64_t)b * N;
+        for (int c = 0; c < kOut; ++c) {
+            const float t = T[o + c * N];
+            const float d = t == t ? (Y[o + c * N] - t) * pore : 0.f;
             f[c] = (float)(2.0 * inv) * d;
             s += (double)d * d;
         }
         uint4* d = reinterpret_cast<uint4*>(gz + r * 32);
         d[0] = pack8(f);
-        f[0] = f[1] = f[2] = 0.f;
+        for (int c = 0; c < kOut; ++c) f[c] = 0.f;
         const uint4 zero = pack8(f);
         d[1] = zero;
         d[2] = zero;
@@ -732,7 +737,8 @@ struct lbm_wsnet {
     cudaStream_t stream = nullptr;
     // activation / gradient buffers of the current (batch, geometry)
     std::map<std::string, void*> buf;
-    int gB = 0, gX = 0, gY = 0, gZ = 0;
+    int gB = 0, gX = 0, gY = 0, gZ = 0;  // current batch and volume
+    int capB = 0;                        // batch the buffers were allocated for
     std::string err;
     int status = LBM_OK;
 };
@@ -769,7 +775,7 @@ int wenter(lbm_wsnet* n) {
 void free_buffers(lbm_wsnet* n) {
     for (auto& kv : n->buf) cudaFree(kv.second);
     n->buf.clear();
-    n->gB = n->gX = n->gY = n->gZ = 0;
+    n->gB = n->gX = n->gY = n->gZ = n->capB = 0;
 }
 
 PGeo level_geo(const lbm_wsnet* n, int l) {
@@ -782,11 +788,19 @@ int chans(const lbm_wsnet* n, int l) { return n->base << l; }
 // `grads`); every buffer starts zeroed so its border rows are zero (no kernel
 // writes a non-zero value there).
 int ensure_buffers(lbm_wsnet* n, int B, int X, int Y, int Z, bool grads) {
-    const bool same = n->gB == B && n->gX == X && n->gY == Y && n->gZ == Z && !n->buf.empty();
-    if (same && (!grads || n->buf.count("gZ"))) return LBM_OK;
+    // a batch no larger than the allocated one reuses the buffers (the rows of
+    // the samples past B are left alone, so every border row stays zero)
+    const bool fits = n->gX == X && n->gY == Y && n->gZ == Z && B <= n->capB && !n->buf.empty();
+    if (fits && (!grads || n->buf.count("gZ"))) {
+        n->gB = B;
+        return LBM_OK;
+    }
     WS_CUDA(n, cudaStreamSynchronize(n->stream));
-    if (!same) free_buffers(n);
-    n->gB = B;
+    if (!fits) {
+        free_buffers(n);
+        n->capB = B;
+    }
+    n->gB = n->capB;  // allocation sizes
     n->gX = X;
     n->gY = Y;
     n->gZ = Z;
@@ -807,9 +821,9 @@ int ensure_buffers(lbm_wsnet* n, int B, int X, int Y, int Z, bool grads) {
     auto act = [&](const std::string& name, int l, int C) { return alloc(name, (size_t)level_geo(n, l).rows() * C * 2); };
     const int Lv = n->levels;
     int rc = LBM_OK;
-    const int64_t vox = (int64_t)B * X * Y * Z;
+    const int64_t vox = (int64_t)n->capB * X * Y * Z;
     if ((rc = act("X", 0, 32))) return rc;
-    if ((rc = alloc("Y", (size_t)vox * 3 * 4))) return rc;
+    if ((rc = alloc("Y", (size_t)vox * wsn::kOut * 4))) return rc;
     if ((rc = alloc("M", (size_t)vox))) return rc;
     for (int l = 0; l < Lv; ++l) {
         const int C = chans(n, l);
@@ -827,9 +841,10 @@ int ensure_buffers(lbm_wsnet* n, int B, int X, int Y, int Z, bool grads) {
         if (l > 0 && (rc = act(nm("gP%d"), l, chans(n, l - 1)))) return rc;
     }
     if (grads) {
-        if ((rc = alloc("T", (size_t)vox * 3 * 4))) return rc;
+        if ((rc = alloc("T", (size_t)vox * wsn::kOut * 4))) return rc;
         if ((rc = act("gZ", 0, 32))) return rc;  // last: its presence marks the gradient buffers
     }
+    n->gB = B;
     return LBM_OK;
 }
 
@@ -943,7 +958,7 @@ int forward(lbm_wsnet* n) {
         below = s1;
         k += 2;
     }
-    // Y = conv(top) * X (3 of the 32 padded output channels)
+    // Y = conv(top) * X (kOut of the 32 padded output channels)
     if ((rc = fwd_layer(n, k, B16(n, below), 0, false, nullptr, nullptr, nullptr, (float*)n->buf.at("Y"),
                         B16(n, "X"))))
         return rc;
@@ -1046,7 +1061,7 @@ int loss_grad_dev(lbm_wsnet* n, int64_t npore, double* loss) {
     WS_CUDA(n, cudaMemsetAsync(n->d_loss, 0, sizeof(double), n->stream));
     wsn::k_mse<<<wsn::gs_blocks((int64_t)g0.B * g0.X * g0.Y * g0.Z), 256, 0, n->stream>>>(
         (const float*)n->buf.at("Y"), (const float*)n->buf.at("T"), B16(n, "X"), B16(n, "gZ"), g0,
-        1.0 / (3.0 * (double)npore), n->d_loss);
+        1.0 / ((double)wsn::kOut * (double)npore), n->d_loss);
     WS_CUDA(n, cudaGetLastError());
     WS_CUDA(n, cudaMemsetAsync(n->g, 0, sizeof(float) * n->np, n->stream));
     if ((rc = backward(n))) return rc;
@@ -1085,7 +1100,7 @@ int lbm_wsnet_create(int levels, int base, lbm_wsnet** out) {
         shp.push_back({base << l, base << (l + 1)});
         shp.push_back({base << l, base << l});
     }
-    shp.push_back({3, base});
+    shp.push_back({wsn::kOut, base});
     int64_t k = 0, w = 0, b = 0;
     for (auto& s : shp) {
         wsn::LayerDesc d{};
@@ -1175,7 +1190,8 @@ int lbm_wsnet_loss_grad(lbm_wsnet* n, const uint8_t* mask, const float* target, 
     const int64_t N0 = (int64_t)nz * ny * nx;
     if ((rc = ensure_buffers(n, batch, nx, ny, nz, true))) return rc;
     WS_CUDA(n, cudaMemcpyAsync(n->buf.at("M"), mask, batch * N0, cudaMemcpyHostToDevice, n->stream));
-    WS_CUDA(n, cudaMemcpyAsync(n->buf.at("T"), target, batch * 3 * N0 * 4, cudaMemcpyHostToDevice, n->stream));
+    WS_CUDA(n, cudaMemcpyAsync(n->buf.at("T"), target, batch * wsn::kOut * N0 * 4, cudaMemcpyHostToDevice,
+                               n->stream));
     double l = 0.0;
     if ((rc = loss_grad_dev(n, count_pores(mask, batch * N0), &l))) return rc;
     if ((rc = check_err(n))) return rc;
@@ -1198,13 +1214,13 @@ int lbm_wsnet_train(lbm_wsnet* n, const uint8_t* masks, const float* targets, in
     uint8_t* dm = nullptr;
     float* dt = nullptr;
     WS_CUDA(n, cudaMalloc(&dm, (size_t)n_samples * N0));
-    cudaError_t e = cudaMalloc(&dt, (size_t)n_samples * 3 * N0 * 4);
+    cudaError_t e = cudaMalloc(&dt, (size_t)n_samples * wsn::kOut * N0 * 4);
     if (e != cudaSuccess) {
         cudaFree(dm);
         return wfail(n, LBM_ENOMEM, "training set: %s", cudaGetErrorString(e));
     }
     e = cudaMemcpy(dm, masks, (size_t)n_samples * N0, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(dt, targets, (size_t)n_samples * 3 * N0 * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dt, targets, (size_t)n_samples * wsn::kOut * N0 * 4, cudaMemcpyHostToDevice);
     double* h_loss = nullptr;
     const int nbatch = (n_samples + batch - 1) / batch;
     if (e == cudaSuccess) e = cudaMallocHost(&h_loss, sizeof(double) * (size_t)epochs * nbatch);
@@ -1220,8 +1236,9 @@ int lbm_wsnet_train(lbm_wsnet* n, const uint8_t* masks, const float* targets, in
                 e = cudaMemcpyAsync((uint8_t*)n->buf.at("M") + (size_t)j * N0, dm + (size_t)idx * N0, N0,
                                     cudaMemcpyDeviceToDevice, n->stream);
                 if (e == cudaSuccess)
-                    e = cudaMemcpyAsync((float*)n->buf.at("T") + (size_t)j * 3 * N0, dt + (size_t)idx * 3 * N0,
-                                        3 * N0 * 4, cudaMemcpyDeviceToDevice, n->stream);
+                    e = cudaMemcpyAsync((float*)n->buf.at("T") + (size_t)j * wsn::kOut * N0,
+                                        dt + (size_t)idx * wsn::kOut * N0, wsn::kOut * N0 * 4,
+                                        cudaMemcpyDeviceToDevice, n->stream);
             }
             if (e != cudaSuccess) break;
             if ((rc = loss_grad_dev(n, np_b, h_loss + (size_t)ep * nbatch + bi))) break;
@@ -1260,7 +1277,7 @@ int lbm_wsnet_predict(lbm_wsnet* n, const uint8_t* mask, int nx, int ny, int nz,
     if ((rc = ensure_buffers(n, 1, nx, ny, nz, false))) return rc;
     WS_CUDA(n, cudaMemcpyAsync(n->buf.at("M"), mask, N0, cudaMemcpyHostToDevice, n->stream));
     if ((rc = forward(n))) return rc;
-    WS_CUDA(n, cudaMemcpyAsync(y, n->buf.at("Y"), 3 * N0 * 4, cudaMemcpyDeviceToHost, n->stream));
+    WS_CUDA(n, cudaMemcpyAsync(y, n->buf.at("Y"), wsn::kOut * N0 * 4, cudaMemcpyDeviceToHost, n->stream));
     return check_err(n);
 }
 
@@ -1292,26 +1309,23 @@ int lbm_wsnet_destroy(lbm_wsnet* n) {
 
 const char* lbm_wsnet_last_error(const lbm_wsnet* n) { return n ? n->err.c_str() : "invalid network handle"; }
 
-int lbm_conv3d_bf16(int op, const void* in, const void* aux, const void* w, const float* bias, int relu, void* out,
-                    int batch, int nx, int ny, int nz, int cin, int cout, void* stream) {
+}  // extern "C"
+
+namespace {
+
+// One convolution on caller buffers, launched `reps` times; with ms != NULL the
+// launches are bracketed by CUDA events on `st` and the mean time returned.
+int conv_call(int op, const void* in, const void* aux, const void* w, const float* bias, int relu, void* out,
+              int batch, int nx, int ny, int nz, int cin, int cout, int reps, float* ms, cudaStream_t st) {
     if (!in || !w || !out || batch < 1 || nx < 1 || ny < 1 || nz < 1 || !wsn::chan_ok(cin) || !wsn::chan_ok(cout) ||
-        op < 0 || op > 2 || (op == 2 && !aux))
+        op < 0 || op > 2 || (op == 2 && !aux) || reps < 1)
         return LBM_EINVAL;
-    cudaStream_t st = (cudaStream_t)stream;
     const PGeo g{batch, nx, ny, nz};
     int* d_err = nullptr;
     if (cudaMalloc(&d_err, sizeof(int)) != cudaSuccess) return LBM_ENOMEM;
     cudaError_t e = cudaMemsetAsync(d_err, 0, sizeof(int), st);
     bf16* wb = nullptr;
-    if (e == cudaSuccess && op == 0) {
-        wsn::ConvEpi ep{};
-        ep.bias = bias;
-        ep.relu = relu;
-        ep.out = (bf16*)out;
-        ep.err = d_err;
-        ep.g = g;
-        e = wsn::conv(cin, cout, (const bf16*)in, (const bf16*)w, ep, st);
-    } else if (e == cudaSuccess && op == 1) {
+    if (e == cudaSuccess && op == 1) {
         // data gradient: flip and transpose the weights into [cin][27][cout]
         std::vector<uint16_t> hw((size_t)cout * 27 * cin), hb(hw.size());
         e = cudaMemcpyAsync(hw.data(), w, hw.size() * 2, cudaMemcpyDeviceToHost, st);
@@ -1322,30 +1336,72 @@ int lbm_conv3d_bf16(int op, const void* in, const void* aux, const void* w, cons
                     hb[((size_t)ci * 27 + (26 - t)) * cout + co] = hw[((size_t)co * 27 + t) * cin + ci];
         if (e == cudaSuccess) e = cudaMalloc(&wb, hb.size() * 2);
         if (e == cudaSuccess) e = cudaMemcpyAsync(wb, hb.data(), hb.size() * 2, cudaMemcpyHostToDevice, st);
-        wsn::ConvEpi ep{};
-        ep.out = (bf16*)out;
-        ep.err = d_err;
-        ep.g = g;
-        if (e == cudaSuccess) e = wsn::conv(cout, cin, (const bf16*)in, wb, ep, st);
-    } else if (e == cudaSuccess) {
-        wsn::WgArgs a{};
-        a.gw = (float*)out;
-        a.cin_real = cin;
-        a.cout_real = cout;
-        a.err = d_err;
-        a.g = g;
-        int dev = 0, nsm = 152;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        e = wsn::wgrad(cin, cout, (const bf16*)in, (const bf16*)aux, a, st, nsm);
     }
+    int dev = 0, nsm = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    if (ms && e == cudaSuccess) e = cudaEventCreate(&ev[0]);
+    if (ms && e == cudaSuccess) e = cudaEventCreate(&ev[1]);
+    if (ms && e == cudaSuccess) e = cudaEventRecord(ev[0], st);
+    for (int r = 0; r < reps && e == cudaSuccess; ++r) {
+        if (op == 0) {
+            wsn::ConvEpi ep{};
+            ep.bias = bias;
+            ep.relu = relu;
+            ep.out = (bf16*)out;
+            ep.err = d_err;
+            ep.g = g;
+            e = wsn::conv(cin, cout, (const bf16*)in, (const bf16*)w, ep, st);
+        } else if (op == 1) {
+            wsn::ConvEpi ep{};
+            ep.out = (bf16*)out;
+            ep.err = d_err;
+            ep.g = g;
+            e = wsn::conv(cout, cin, (const bf16*)in, wb, ep, st);
+        } else {
+            wsn::WgArgs a{};
+            a.gw = (float*)out;
+            a.cin_real = cin;
+            a.cout_real = cout;
+            a.err = d_err;
+            a.g = g;
+            e = wsn::wgrad(cin, cout, (const bf16*)in, (const bf16*)aux, a, st, nsm);
+        }
+    }
+    if (ms && e == cudaSuccess) e = cudaEventRecord(ev[1], st);
     int h = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (ms && e == cudaSuccess) {
+        float t = 0.f;
+        e = cudaEventElapsedTime(&t, ev[0], ev[1]);
+        *ms = t / reps;
+    }
+    for (auto& x : ev)
+        if (x) cudaEventDestroy(x);
     cudaFree(d_err);
     if (wb) cudaFree(wb);
     if (e != cudaSuccess) return LBM_ECUDA;
     return h ? LBM_ETIMEOUT : LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_conv3d_bf16(int op, const void* in, const void* aux, const void* w, const float* bias, int relu, void* out,
+                    int batch, int nx, int ny, int nz, int cin, int cout, void* stream) {
+    return conv_call(op, in, aux, w, bias, relu, out, batch, nx, ny, nz, cin, cout, 1, nullptr,
+                     (cudaStream_t)stream);
+}
+
+int lbm_conv3d_bf16_time(int op, const void* in, const void* aux, const void* w, const float* bias, int relu,
+                         void* out, int batch, int nx, int ny, int nz, int cin, int cout, int reps, float* ms,
+                         void* stream) {
+    if (!ms) return LBM_EINVAL;
+    return conv_call(op, in, aux, w, bias, relu, out, batch, nx, ny, nz, cin, cout, reps, ms,
+                     (cudaStream_t)stream);
 }
 
 }  // extern "C"

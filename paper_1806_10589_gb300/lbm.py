@@ -100,6 +100,8 @@ SIGNATURES = {
     "lbm_wsnet_last_error": (C.c_char_p, [_P]),
     "lbm_conv3d_bf16": (C.c_int, [C.c_int, _P, _P, _P, _FP, C.c_int, _P, C.c_int, C.c_int, C.c_int, C.c_int,
                                   C.c_int, C.c_int, _P]),
+    "lbm_conv3d_bf16_time": (C.c_int, [C.c_int, _P, _P, _P, _FP, C.c_int, _P, C.c_int, C.c_int, C.c_int, C.c_int,
+                                       C.c_int, C.c_int, C.c_int, _FP, _P]),
 }
 
 _lib = None
@@ -383,7 +385,9 @@ class Batch:
 class WarmStartNet:
     """The warm-start network (lbm_wsnet_*): `levels` resolution levels with
     base * 2^l channels at level l (the specified network: 4 levels, 32 base
-    channels)."""
+    channels); 4 output fields: u / u_D and the pressure gradient G."""
+
+    N_OUT = 4
 
     def __init__(self, levels=4, base=32, stream=None):
         lib = load_library()
@@ -422,7 +426,7 @@ class WarmStartNet:
             shapes += [(c[l], c[l - 1]), (c[l], c[l])]
         for l in range(self.levels - 2, -1, -1):
             shapes += [(c[l], c[l + 1]), (c[l], c[l])]
-        return shapes + [(3, c[0])]
+        return shapes + [(self.N_OUT, c[0])]
 
     def set_params(self, p):
         p = np.ascontiguousarray(p, dtype=np.float32)
@@ -439,6 +443,8 @@ class WarmStartNet:
         masks = np.ascontiguousarray(masks, dtype=np.uint8)
         targets = np.ascontiguousarray(targets, dtype=np.float32)
         B, nz, ny, nx = masks.shape
+        if targets.shape != (B, self.N_OUT, nz, ny, nx):
+            raise ValueError("targets must have shape %s" % ((B, self.N_OUT, nz, ny, nx),))
         loss = C.c_double()
         g = np.empty(self.n_params, np.float32)
         self._check(self._lib.lbm_wsnet_loss_grad(self._h, _ptr(masks, C.c_uint8), _ptr(targets, C.c_float), B,
@@ -449,6 +455,8 @@ class WarmStartNet:
         masks = np.ascontiguousarray(masks, dtype=np.uint8)
         targets = np.ascontiguousarray(targets, dtype=np.float32)
         S, nz, ny, nx = masks.shape
+        if targets.shape != (S, self.N_OUT, nz, ny, nx):
+            raise ValueError("targets must have shape %s" % ((S, self.N_OUT, nz, ny, nx),))
         rng = np.random.default_rng(seed)
         order = np.ascontiguousarray(np.concatenate([rng.permutation(S) for _ in range(epochs)]).astype(np.int32))
         hist = np.empty(epochs, np.float32)
@@ -460,7 +468,7 @@ class WarmStartNet:
     def predict(self, mask):
         mask = np.ascontiguousarray(mask, dtype=np.uint8)
         nz, ny, nx = mask.shape
-        y = np.empty((3, nz, ny, nx), np.float32)
+        y = np.empty((self.N_OUT, nz, ny, nx), np.float32)
         self._check(self._lib.lbm_wsnet_predict(self._h, _ptr(mask, C.c_uint8), nx, ny, nz, _ptr(y, C.c_float)))
         return y
 
@@ -468,15 +476,23 @@ class WarmStartNet:
         self._check(self._lib.lbm_wsnet_release_buffers(self._h))
 
 
-def conv3d_bf16(op, inp, aux, w, bias, relu, out, batch, nx, ny, nz, cin, cout, stream=None):
-    """lbm_conv3d_bf16 on device pointers (ints, e.g. torch tensor.data_ptr())."""
+def conv3d_bf16(op, inp, aux, w, bias, relu, out, batch, nx, ny, nz, cin, cout, stream=None, reps=None):
+    """lbm_conv3d_bf16 on device pointers (ints, e.g. torch tensor.data_ptr());
+    with reps, lbm_conv3d_bf16_time: returns the mean ms of one launch."""
     lib = load_library()
     hs = getattr(stream, "cuda_stream", stream) if stream is not None else None
-    st = lib.lbm_conv3d_bf16(int(op), _P(inp), _P(aux) if aux else None, _P(w),
-                             C.cast(_P(bias), _FP) if bias else None, int(relu), _P(out), int(batch), int(nx),
-                             int(ny), int(nz), int(cin), int(cout), _P(hs) if hs else None)
+    args = [int(op), _P(inp), _P(aux) if aux else None, _P(w), C.cast(_P(bias), _FP) if bias else None, int(relu),
+            _P(out), int(batch), int(nx), int(ny), int(nz), int(cin), int(cout)]
+    if reps is None:
+        st = lib.lbm_conv3d_bf16(*args, _P(hs) if hs else None)
+        ms = None
+    else:
+        t = C.c_float()
+        st = lib.lbm_conv3d_bf16_time(*args, int(reps), C.byref(t), _P(hs) if hs else None)
+        ms = t.value
     if st != LBM_OK:
         raise LBMError(st, "lbm_conv3d_bf16(op %d, cin %d, cout %d)" % (op, cin, cout))
+    return ms
 
 
 class ColorLattice:

@@ -206,21 +206,44 @@ def test_16bit_deviation_storage_error(torch_cuda, prec, bits):
     assert err <= bound, (err, bound)
 
 
-@pytest.mark.parametrize("variant", [0, 3])
-def test_full_size_sphere_pack_fp32_one_step(torch_cuda, variant):
-    """256^3 sphere pack (radii U[6,12], porosity 0.35, 6 reservoir layers), the
-    benchmark's FP32 configuration, 2 steps from a seeded perturbed state, all
-    cells against the oracle.  Variant 3 is the benchmark's launch shape (AA
-    pattern: layout swap, one gather-scatter and one node-local launch, swap
-    back); variant 0 the library default (two buffers)."""
+@pytest.fixture(scope="module")
+def full_pack():
+    """The benchmark workload (256^3 sphere pack, radii U[6,12], porosity 0.35, 6
+    reservoir layers, tau 0.7, Q = 1e-4 A) from a seeded perturbed state, and the
+    oracle's state after 2 steps (computed once for every format and variant)."""
     m, info = sphere_pack(256, 6, 12, 0.35, seed=2024, reservoir=6)
-    A = int((m[0] == 0).sum())
+    Q = 1e-4 * int((m[0] == 0).sum())
     N = 2
-    got, ref, (q_in, _), _ = _run_pair(m, 0.7, "mrt", "fp32", N, torch_cuda, Q=1e-4 * A, seed=77,
-                                       amp=0.001, variant=variant)
-    d_ref = ref.f - O.W[:, None, None, None] * (m == 0)
-    err = np.abs(got - ref.f).max()
-    assert err <= 20 * N * EPS32 * np.abs(d_ref).max() + 4 * EPS32 * 1e-2, err
+    f0 = _f0(m, 77, 0.001)
+    ref = O.D3Q19Oracle(m, 0.7, "mrt", Q=Q)
+    ref.set_distributions(f0)
+    ref.step(N)
+    return m, Q, N, f0, ref
+
+
+@pytest.mark.parametrize("variant", [0, 3])
+@pytest.mark.parametrize("prec", ["fp32", "fp16dev", "bf16dev"])
+def test_full_size_sphere_pack_two_steps(torch_cuda, full_pack, prec, variant):
+    """The benchmark's workload at full size, every cell against the oracle after
+    2 steps, in every storage format the benchmark reports, on the AA pattern
+    the benchmark times (variant 3: layout swap, one gather-scatter and one
+    node-local launch, swap back) and on the two-buffer kernel (variant 0), at
+    the stated bounds: FP32 20 N eps32 max|d|, FP16 / BF16 8 N 2^-p max|d|."""
+    m, Q, N, f0, ref = full_pack
+    with _lat(m, 0.7, "mrt", prec, torch_cuda) as lat:
+        lat.set_kernel(variant)
+        lat.set_flux_bc(Q)
+        lat.set_distributions(f0)
+        lat.step(N)
+        got = lat.distributions()
+    dmax = float(np.abs(ref.f - O.W[:, None, None, None] * (m == 0)).max())
+    err = float(np.abs(got - ref.f).max())
+    if prec == "fp32":
+        bound = 20 * N * EPS32 * dmax + 4 * EPS32 * 1e-2
+    else:
+        bound = 8 * N * 2.0 ** -(11 if prec == "fp16dev" else 8) * dmax
+    assert np.isfinite(got).all()
+    assert err <= bound, (prec, variant, err, bound)
 
 
 def test_steady_residual_matches_oracle(torch_cuda):

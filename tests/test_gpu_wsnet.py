@@ -161,7 +161,8 @@ def test_loss_and_gradient_match_oracle(net):
     rng = np.random.default_rng(2)
     B, shape = 2, (16, 8, 8)
     masks = (rng.random((B,) + shape) < 0.35).astype(np.uint8)
-    targets = rng.standard_normal((B, 3) + shape).astype(np.float32)
+    targets = rng.standard_normal((B, N.NOUT) + shape).astype(np.float32)
+    targets[:, 3][rng.random((B,) + shape) < 0.3] = np.nan  # entries without a target
     p = _he(4, 32, 12)
     net.set_params(p)
     loss, g = net.loss_grad(masks, targets)
@@ -187,7 +188,8 @@ def test_training_reduces_loss(net):
     rng = np.random.default_rng(5)
     masks = (rng.random((6, 8, 8, 8)) < 0.3).astype(np.uint8)
     pore = 1.0 - masks.astype(np.float32)
-    t = np.stack([pore * 0.5, pore * -0.2, pore * (1.0 + 0.1 * np.arange(8)[None, :, None, None])], axis=1)
+    t = np.stack([pore * 0.5, pore * -0.2, pore * (1.0 + 0.1 * np.arange(8)[None, :, None, None]), pore * 2.0],
+                 axis=1)
     net.set_params(_he(4, 32, 3) * 0.5)
     hist = net.train(masks, t.astype(np.float32), epochs=60, batch=3, lr=1e-3, seed=1)
     assert np.isfinite(hist).all()
@@ -204,7 +206,12 @@ def test_warm_start_pipeline_small(net, torch):
     st = torch.cuda.current_stream()
     masks = [sphere_pack(32, 5.0, 8.0, 0.4, seed=300 + k, cache=False)[0] for k in range(8)]
     targets, ks = ws.steady_targets(Batch, masks, 0.8, 1e-4, 3000, stream=st)
-    assert np.isfinite(targets).all() and (ks > 0).all()
+    assert np.isfinite(targets[:, :3]).all() and (ks > 0).all()
+    # G is defined (finite) exactly where a pore voxel's +z neighbour is a pore
+    m = np.stack(masks)
+    defined = np.zeros(m.shape, bool)
+    defined[:, :-1] = (m[:, :-1] == 0) & (m[:, 1:] == 0)
+    np.testing.assert_array_equal(np.isfinite(targets[:, 3]), defined)
     c_kc = ws.fit_kc(masks, ks)
     assert c_kc > 0
     net.set_params(ws.he_init(net, 0))
@@ -219,3 +226,50 @@ def test_warm_start_pipeline_small(net, torch):
     info = {"res": res, "k_ref": ref["k"]}
     assert res["cold"]["reached"] and res["warm"]["reached"], info
     assert abs(res["warm"]["k"] - ref["k"]) <= 1e-3 * ref["k"]
+
+
+def test_adam_steps_match_the_published_update(torch):
+    """Two training steps (one batch holding every sample, so each epoch is
+    one step) against Adam as Kingma and Ba define it, fed with the gradients
+    the library reports at the same parameters: m = b1 m + (1 - b1) g,
+    v = b2 v + (1 - b2) g^2, p -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps).
+    The weight gradients are FP32 atomic sums whose order varies between
+    calls, so only parameters whose gradient is well above that noise
+    (|g| > 1e-3 of the layer's max|g| in both steps) are compared, at 2e-3 of
+    the step size."""
+    from paper_1806_10589_gb300 import WarmStartNet
+
+    rng = np.random.default_rng(8)
+    masks = (rng.random((2, 8, 8, 8)) < 0.3).astype(np.uint8)
+    t = rng.standard_normal((2, N.NOUT, 8, 8, 8)).astype(np.float32)
+    lr, b1, b2, eps = 1e-3, 0.9, 0.999, 1e-8
+    with_net = WarmStartNet(2, 32, stream=torch.cuda.current_stream())
+    try:
+        p0 = _he(2, 32, 21)
+        with_net.set_params(p0)
+        _, g0 = with_net.loss_grad(masks, t)
+        with_net.train(masks, t, epochs=1, batch=2, lr=lr, seed=0)
+        p1 = with_net.params()
+        _, g1 = with_net.loss_grad(masks, t)
+        # a second epoch continues the same Adam state
+        with_net.train(masks, t, epochs=1, batch=2, lr=lr, seed=0)
+        p2 = with_net.params()
+    finally:
+        with_net.close()
+    g0, g1 = g0.astype(np.float64), g1.astype(np.float64)
+    m1, v1 = (1 - b1) * g0, (1 - b2) * g0 ** 2
+    want1 = p0 - lr * (m1 / (1 - b1)) / (np.sqrt(v1 / (1 - b2)) + eps)
+    m2, v2 = b1 * m1 + (1 - b1) * g1, b2 * v1 + (1 - b2) * g1 ** 2
+    want2 = p1 - lr * (m2 / (1 - b1 ** 2)) / (np.sqrt(v2 / (1 - b2 ** 2)) + eps)
+    # "well above the noise": per layer (gradient scales differ by orders of magnitude between layers)
+    big = np.zeros(g0.size, bool)
+    k = 0
+    for co, ci in N.layer_shapes(2, 32):
+        sl = slice(k, k + co * 27 * ci + co)
+        big[sl] = (np.abs(g0[sl]) > 1e-3 * np.abs(g0[sl]).max()) & (np.abs(g1[sl]) > 1e-3 * np.abs(g1[sl]).max())
+        k = sl.stop
+    assert big.sum() > 0.5 * big.size
+    assert np.abs(p1 - want1)[big].max() <= 2e-3 * lr
+    assert np.abs(p2 - want2)[big].max() <= 2e-3 * lr
+    # the first step moves every parameter by lr |g| / (|g| + eps) <= lr
+    assert np.abs(p1 - p0).max() <= lr * (1 + 1e-3)

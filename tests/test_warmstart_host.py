@@ -79,3 +79,39 @@ def test_he_init_layout_and_spread():
         assert abs(w.std() / target - 1) < 5 / math.sqrt(2 * w.size)
         k += co * ci * 27 + co
     assert k == p.size
+
+
+def test_pressure_profile_inverts_the_gradient_target():
+    """For a density that depends on z only, in an open box, the plane means of
+    the gradient target summed from the outlet give back rho(z) exactly; voxels
+    whose +z neighbour is solid carry no target (NaN)."""
+    nz, ny, nx = 9, 4, 5
+    m = np.zeros((nz, ny, nx), np.uint8)
+    rng = np.random.default_rng(2)
+    rho_z = 1.0 + np.cumsum(rng.random(nz))[::-1] * 1e-3
+    rho_z = rho_z - rho_z[-1] + 1.0
+    rho = rho_z[:, None, None] * np.ones(m.shape)
+    Q, tau = 0.02, 0.8
+    G = ws.gradient_target(rho, m, Q, tau)
+    assert np.isnan(G[-1]).all() and not np.isnan(G[:-1]).any()
+    np.testing.assert_allclose(ws.pressure_profile(G, m, Q, tau), rho_z, rtol=0, atol=1e-14)
+    m2 = m.copy()
+    m2[3, 1, 1] = 1
+    G2 = ws.gradient_target(rho, m2, Q, tau)
+    assert np.isnan(G2[2, 1, 1]) and np.isnan(G2[3, 1, 1])
+    np.testing.assert_allclose(ws.pressure_profile(G2, m2, Q, tau), rho_z, rtol=0, atol=1e-14)
+
+
+def test_kc_profile_is_the_darcy_ramp():
+    m = np.zeros((6, 5, 5), np.uint8)
+    m[2, 2, 2] = 1
+    Q, tau, c = 0.01, 0.7, 0.2
+    prof = ws.kc_profile(m, Q, tau, c)
+    k_est = c * ws.kc_features(m)[2]
+    nu = (tau - 0.5) / 3.0
+    dp = nu * Q / 25.0 * 5 / k_est
+    np.testing.assert_allclose(prof, 1.0 + 3.0 * dp * (1 - np.arange(6) / 5.0), rtol=1e-14)
+    # the permeability the 0.1 % rule reads off this profile is the Kozeny-Carman estimate
+    # (rho_in - 1 is ~6e-8 here, so its FP64 rounding is ~2e-9 relative)
+    from paper_1806_10589_gb300 import convergence as cv
+    assert math.isclose(cv.permeability(Q, m.shape, tau, prof[0], prof[-1]), k_est, rel_tol=1e-7)

@@ -3,7 +3,7 @@ n-dimensional correlation, pooling/upsampling backward are the adjoints of
 the forward maps, the parameter packing round-trips, the specified network
 (4 levels, 32 base channels) has the stated layer shapes, and the
 hand-written backward pass equals central finite differences of the forward
-pass at every depth."""
+pass at every depth (with entries that have no target)."""
 import numpy as np
 import pytest
 
@@ -52,7 +52,7 @@ def test_pack_unpack_roundtrip_and_layout():
 def test_specified_network_shapes():
     shapes = N.layer_shapes(4, 32)
     assert len(shapes) == 15
-    assert shapes[0] == (32, 1) and shapes[-1] == (3, 32)
+    assert shapes[0] == (32, 1) and shapes[-1] == (4, 32)
     assert [co for co, _ in shapes[:8:2]] == [32, 64, 128, 256]
     assert shapes[8] == (128, 256) and shapes[12] == (32, 64)
     assert N.n_params(4, 32) == sum(co * ci * 27 + co for co, ci in shapes)
@@ -62,7 +62,8 @@ def test_specified_network_shapes():
 def test_backward_matches_finite_differences(levels, base, side):
     rng = np.random.default_rng(2 + levels)
     pore = (rng.random((side, side, side)) > 0.3).astype(float)
-    target = rng.standard_normal((3, side, side, side))
+    target = rng.standard_normal((N.NOUT, side, side, side))
+    target[3][rng.random(target[3].shape) < 0.3] = np.nan  # entries without a target
     p = rng.standard_normal(N.n_params(levels, base)) * 0.3
     loss, g = N.loss_and_grad(p, pore, target, levels, base)
     # sample parameters from every layer
@@ -88,3 +89,18 @@ def test_output_is_zero_in_solids():
     p = rng.standard_normal(N.n_params(3, 2))
     Y = N.forward(p, pore, 3, 2)
     assert np.all(Y[:, pore == 0] == 0.0)
+
+
+def test_entries_without_target_add_nothing():
+    """A NaN target entry is the same as leaving that entry out of the sum:
+    the loss equals the plain masked sum over the other entries."""
+    rng = np.random.default_rng(6)
+    pore = (rng.random((4, 4, 4)) > 0.3).astype(float)
+    p = rng.standard_normal(N.n_params(2, 2)) * 0.3
+    t = rng.standard_normal((N.NOUT, 4, 4, 4))
+    t[3, 1:3] = np.nan
+    loss, _ = N.loss_and_grad(p, pore, t, 2, 2)
+    Y = N.forward(p, pore, 2, 2)
+    keep = ~np.isnan(t) & (pore[None] > 0)
+    want = float(((Y - np.nan_to_num(t)) ** 2)[keep].sum()) / (N.NOUT * pore.sum())
+    assert abs(loss - want) <= 1e-12 * want
