@@ -4,14 +4,23 @@ initial field f = f^eq(rho, u) (host orchestration only; the LBM, the network
 forward/backward/Adam and the equilibrium initialisation run in the CUDA
 library).
 
-The network predicts, per voxel, u / u_D (u_D = Q / (nx ny)) and the local
-pressure gradient G = -(p(z+1) - p(z)) / (nu u_D), p = c_s^2 rho.  Initial
-fields of a new geometry with flux Q:
+The network predicts, per pore voxel, u / u_D (u_D = Q / (nx ny)) and
+G_SCALE * H, H = phi(z) (pbar(z) - pbar(z+1)) / (nu u_D): the drop of the
+plane-mean pressure pbar (the mean of p = c_s^2 rho over the pore voxels of a
+plane) from the voxel's plane to the next, times the plane's porosity phi(z)
+(its pore fraction).  H is a property of the plane that each voxel estimates
+from the geometry it sees; the porosity factor removes most of the spread of
+the drop itself, which is large across planes with few pores (the mean
+interstitial velocity there is u_D / phi).  (A local vertical pressure
+difference averaged over vertically connected pores misses the plane-mean drop
+by a factor of about two in these packs, so it is not used.)  The sum of the
+drops is the whole pressure drop, so these targets reproduce the steady state's
+permeability exactly.  G_SCALE makes the squared errors of H weigh about as
+much as those of the velocity.  Initial fields of a new geometry with flux Q:
   u = u_D * net_u(mask)                                       (network velocity)
-  rho(z) = rho_out + (nu u_D / c_s^2) sum_{z' >= z} Gbar(z')   (network pressure)
-with Gbar(z) the mean of the predicted G over the pore voxels of plane z whose
-+z neighbour is a pore (the voxels where G is defined); or, without the
-network, the analytic ramp
+  rho(z) = rho_out + (nu u_D / c_s^2) sum_{z' >= z} Hbar(z') / phi(z')
+with Hbar(z) the mean over the pore voxels of plane z of the predicted H
+(network pressure); or, without the network, the analytic ramp
   rho(z) = rho_out + dp_est * (1 - z / (nz - 1)) / c_s^2,
   dp_est = nu u_D (nz - 1) / k_est,  k_est = c_KC phi^3 / (S^2 (1 - phi)^2)
 (Darcy with Kozeny-Carman), phi the porosity, S the pore-solid face count per
@@ -27,6 +36,7 @@ import numpy as np
 from . import convergence as cv
 
 CS2 = 1.0 / 3.0
+G_SCALE = 4.0
 
 
 def he_init(net, seed):
@@ -60,24 +70,41 @@ def kc_features(mask):
     return phi, S, phi ** 3 / (S * S * (1.0 - phi) ** 2)
 
 
-def gradient_target(rho, mask, Q, tau):
-    """G = -c_s^2 (rho(z+1) - rho(z)) / (nu u_D) on pore voxels whose +z
-    neighbour is a pore; NaN (no target) elsewhere and on the last plane."""
+def plane_means(field, mask):
+    """Mean of field over the pore voxels of each z plane (0 for a plane without pores)."""
+    pore = mask == 0
+    cnt = pore.reshape(mask.shape[0], -1).sum(axis=1)
+    tot = np.where(pore, field, 0.0).reshape(mask.shape[0], -1).sum(axis=1)
+    return np.where(cnt > 0, tot / np.maximum(cnt, 1), 0.0)
+
+
+def plane_porosity(mask):
+    return (mask == 0).reshape(mask.shape[0], -1).mean(axis=1)
+
+
+def drop_target(rho, mask, Q, tau):
+    """G_SCALE phi(z) (pbar(z) - pbar(z+1)) / (nu u_D) on the pore voxels of
+    plane z, z < nz - 1; NaN (no target) at solids and on the last plane."""
     nz, ny, nx = mask.shape
     nu = CS2 * (tau - 0.5)
     uD = Q / (nx * ny)
-    G = np.full(mask.shape, np.nan)
-    ok = (mask[:-1] == 0) & (mask[1:] == 0)
-    G[:-1][ok] = (-CS2 * (rho[1:] - rho[:-1]) / (nu * uD))[ok]
-    return G
+    pbar = CS2 * plane_means(rho, mask)
+    drop = np.append(G_SCALE * plane_porosity(mask)[:-1] * (pbar[:-1] - pbar[1:]) / (nu * uD), np.nan)
+    return np.where(mask == 0, drop[:, None, None], np.nan)
 
 
-def steady_targets(batch_cls, masks, tau, u_mean, steps, precision="fp32", stream=None):
+def steady_targets(batch_cls, masks, tau, u_mean, steps, precision="fp32", stream=None, margin=0):
     """Run every geometry to (near) steady state in one batched ensemble and
-    return (targets as float32 [S][4][z][y][x]: u / u_D and G, permeabilities)."""
+    return (inputs, targets, permeabilities): with margin > 0 the inputs and
+    targets are the interior crops mask[m:-m, m:-m, m:-m] (no lateral walls and
+    no inlet or outlet planes inside them), else the whole boxes; targets are
+    float32 [S][4][z][y][x] (u / u_D and G_SCALE H, u_D = Q / (nx ny) of the
+    whole box); the permeabilities are the whole boxes'."""
     S = len(masks)
     Qs = [u_mean * int((m[0] == 0).sum()) for m in masks]
-    targets = np.zeros((S, 4) + masks[0].shape, np.float32)
+    sl = (slice(margin, -margin),) * 3 if margin > 0 else (slice(None),) * 3
+    inputs = [np.ascontiguousarray(m[sl]) for m in masks]
+    targets = np.zeros((S, 4) + inputs[0].shape, np.float32)
     ks = np.zeros(S)
     with batch_cls(masks, tau, "mrt", precision, stream=stream) as b:
         for k, q in enumerate(Qs):
@@ -87,11 +114,14 @@ def steady_targets(batch_cls, masks, tau, u_mean, steps, precision="fp32", strea
             rho, ux, uy, uz = b.fields(k)
             nz, ny, nx = m.shape
             uD = Qs[k] / (nx * ny)
-            targets[k, :3] = (np.stack([ux, uy, uz]) / uD).astype(np.float32)
-            targets[k, 3] = gradient_target(rho, m, Qs[k], tau).astype(np.float32)
+            targets[k, :3] = (np.stack([ux[sl], uy[sl], uz[sl]]) / uD).astype(np.float32)
+            # drop_target's u_D is Q / (area of the box it is given): hand it the
+            # whole box's u_D through an equivalent flux
+            cz, cy, cx = inputs[k].shape
+            targets[k, 3] = drop_target(rho[sl], inputs[k], uD * cx * cy, tau).astype(np.float32)
             _, rho_in = b.get_flux(k, 4)
             ks[k] = cv.permeability(Qs[k], m.shape, tau, rho_in, 1.0)
-    return targets, ks
+    return inputs, targets, ks
 
 
 def fit_kc(masks, ks):
@@ -101,15 +131,14 @@ def fit_kc(masks, ks):
 
 
 def pressure_profile(G, mask, Q, tau, rho_out=1.0):
-    """rho(z) from a predicted gradient field: the plane means Gbar(z) over the
-    voxels where G is defined, summed from the outlet."""
+    """rho(z) from a predicted drop field (G_SCALE H): its plane means over the
+    pore voxels, divided by the plane porosity, summed from the outlet."""
     nz, ny, nx = mask.shape
     nu = CS2 * (tau - 0.5)
     uD = Q / (nx * ny)
-    ok = (mask[:-1] == 0) & (mask[1:] == 0)
-    cnt = ok.reshape(nz - 1, -1).sum(axis=1)
-    gsum = np.where(ok, G[:-1], 0.0).reshape(nz - 1, -1).sum(axis=1)
-    gbar = np.where(cnt > 0, gsum / np.maximum(cnt, 1), 0.0)
+    phi = plane_porosity(mask)[:-1]
+    hbar = plane_means(np.asarray(G, dtype=np.float64), mask)[:-1] / G_SCALE
+    gbar = np.where(phi > 0, hbar / np.maximum(phi, 1e-300), 0.0)
     drop = np.concatenate([np.cumsum(gbar[::-1])[::-1], [0.0]])  # sum over z' >= z of Gbar(z')
     return rho_out + (nu * uD / CS2) * drop
 

@@ -196,6 +196,32 @@ def test_training_reduces_loss(net):
     assert hist[-1] < 0.2 * hist[0], hist[[0, -1]]
 
 
+def test_interior_crops_of_the_training_data(torch):
+    """With a margin the inputs and targets are the interior crops of the
+    steady states: the crop's velocity is the whole box's (over u_D of the
+    whole box), and its plane drops add up to the pressure difference between
+    the crop's first and last planes."""
+    from lbm_inputs import sphere_pack
+    from paper_1806_10589_gb300 import Batch, Lattice, warmstart as ws
+
+    st = torch.cuda.current_stream()
+    m = sphere_pack(24, 3.0, 5.0, 0.4, seed=41, cache=False)[0]
+    inputs, targets, ks = ws.steady_targets(Batch, [m], 0.8, 1e-4, 600, stream=st, margin=4)
+    assert inputs[0].shape == (16, 16, 16)
+    np.testing.assert_array_equal(inputs[0], m[4:-4, 4:-4, 4:-4])
+    Q = 1e-4 * int((m[0] == 0).sum())
+    uD = Q / 24 ** 2
+    with Lattice(m, 0.8, "mrt", "fp32", stream=st) as lat:
+        lat.set_flux_bc(Q)
+        lat.step(600)
+        rho, ux, uy, uz = lat.fields()
+    c = (slice(4, -4),) * 3
+    np.testing.assert_allclose(targets[0, 2], (uz[c] / uD).astype(np.float32), rtol=1e-5, atol=1e-6)
+    prof = ws.pressure_profile(targets[0, 3], inputs[0], uD * 16 * 16, 0.8, rho_out=0.0)
+    pbar = ws.plane_means(rho[c], inputs[0])
+    np.testing.assert_allclose(prof[0] - prof[-1], pbar[0] - pbar[-1], rtol=1e-4)
+
+
 def test_warm_start_pipeline_small(net, torch):
     """End to end at small scale: steady targets from the batched LBM, a short
     training run, Kozeny-Carman calibration and a warm-started lattice that
@@ -205,17 +231,25 @@ def test_warm_start_pipeline_small(net, torch):
 
     st = torch.cuda.current_stream()
     masks = [sphere_pack(32, 5.0, 8.0, 0.4, seed=300 + k, cache=False)[0] for k in range(8)]
-    targets, ks = ws.steady_targets(Batch, masks, 0.8, 1e-4, 3000, stream=st)
+    inputs, targets, ks = ws.steady_targets(Batch, masks, 0.8, 1e-4, 3000, stream=st)
+    assert all(a.shape == m.shape for a, m in zip(inputs, masks))
     assert np.isfinite(targets[:, :3]).all() and (ks > 0).all()
-    # G is defined (finite) exactly where a pore voxel's +z neighbour is a pore
+    # G is defined (finite) on the pore voxels of every plane but the last, and
+    # its plane drops add up to the steady pressure drop: the permeability they
+    # imply is the one the LBM reports
     m = np.stack(masks)
     defined = np.zeros(m.shape, bool)
-    defined[:, :-1] = (m[:, :-1] == 0) & (m[:, 1:] == 0)
+    defined[:, :-1] = m[:, :-1] == 0
     np.testing.assert_array_equal(np.isfinite(targets[:, 3]), defined)
+    for k in range(len(masks)):
+        Q = 1e-4 * int((masks[k][0] == 0).sum())
+        prof = ws.pressure_profile(targets[k, 3], masks[k], Q, 0.8)
+        k_t = cv.permeability(Q, masks[k].shape, 0.8, prof[0], prof[-1])
+        assert abs(k_t - ks[k]) <= 1e-4 * ks[k], (k, k_t, ks[k])
     c_kc = ws.fit_kc(masks, ks)
     assert c_kc > 0
     net.set_params(ws.he_init(net, 0))
-    hist = net.train(np.stack(masks), targets, epochs=20, batch=4, lr=1e-3, seed=0)
+    hist = net.train(np.stack(inputs), targets, epochs=20, batch=4, lr=1e-3, seed=0)
     assert hist[-1] < hist[0]
     m = sphere_pack(32, 5.0, 8.0, 0.4, seed=999, cache=False)[0]
     Q = 1e-4 * int((m[0] == 0).sum())

@@ -81,25 +81,27 @@ def test_he_init_layout_and_spread():
     assert k == p.size
 
 
-def test_pressure_profile_inverts_the_gradient_target():
-    """For a density that depends on z only, in an open box, the plane means of
-    the gradient target summed from the outlet give back rho(z) exactly; voxels
-    whose +z neighbour is solid carry no target (NaN)."""
+def test_pressure_profile_inverts_the_drop_target():
+    """For any density field, the predicted-drop profile built from the exact
+    targets gives back the plane-mean density of every plane (the outlet
+    plane's mean as rho_out); targets exist on the pore voxels of every plane
+    but the last."""
     nz, ny, nx = 9, 4, 5
-    m = np.zeros((nz, ny, nx), np.uint8)
     rng = np.random.default_rng(2)
-    rho_z = 1.0 + np.cumsum(rng.random(nz))[::-1] * 1e-3
-    rho_z = rho_z - rho_z[-1] + 1.0
-    rho = rho_z[:, None, None] * np.ones(m.shape)
+    m = (rng.random((nz, ny, nx)) < 0.3).astype(np.uint8)
+    m[:, 0, 0] = 0  # a pore in every plane
+    rho = 1.0 + 1e-3 * rng.random(m.shape)
     Q, tau = 0.02, 0.8
-    G = ws.gradient_target(rho, m, Q, tau)
-    assert np.isnan(G[-1]).all() and not np.isnan(G[:-1]).any()
-    np.testing.assert_allclose(ws.pressure_profile(G, m, Q, tau), rho_z, rtol=0, atol=1e-14)
-    m2 = m.copy()
-    m2[3, 1, 1] = 1
-    G2 = ws.gradient_target(rho, m2, Q, tau)
-    assert np.isnan(G2[2, 1, 1]) and np.isnan(G2[3, 1, 1])
-    np.testing.assert_allclose(ws.pressure_profile(G2, m2, Q, tau), rho_z, rtol=0, atol=1e-14)
+    G = ws.drop_target(rho, m, Q, tau)
+    defined = np.zeros(m.shape, bool)
+    defined[:-1] = m[:-1] == 0
+    np.testing.assert_array_equal(np.isfinite(G), defined)
+    pbar = ws.plane_means(rho, m)
+    np.testing.assert_allclose(ws.pressure_profile(G, m, Q, tau, rho_out=pbar[-1]), pbar, rtol=0, atol=1e-14)
+    # the drop is constant over a plane's pores
+    for z in range(nz - 1):
+        vals = G[z][m[z] == 0]
+        assert np.ptp(vals) == 0.0
 
 
 def test_kc_profile_is_the_darcy_ramp():
