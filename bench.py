@@ -870,7 +870,7 @@ def conv_roofline(stream, side=64, batch=8, reps=20):
             "frac": per[top]["frac"], "kernel": "k_conv<32,32> / k_wgrad<32,32>", "traffic": None}
 
 
-def run_warmstart_leg(stream, samples=512, side=64, lbm_steps=8000, epochs=30, test_side=256, variant=3,
+def run_warmstart_leg(stream, samples=512, side=64, lbm_steps=8000, epochs=40, test_side=256, variant=3,
                       ref_steps=300000, margin=8):
     """Learned warm start: train the network (4 levels, 32 base channels) on LBM
     steady states of seeded sphere packs (radii U[8,16], porosity U[0.25,0.45])
@@ -907,6 +907,8 @@ def run_warmstart_leg(stream, samples=512, side=64, lbm_steps=8000, epochs=30, t
     t_train = time.perf_counter() - t0
     val_loss = float(np.mean([net.loss_grad(np.stack(masks[j:j + 1]), targets[j:j + 1])[0]
                               for j in range(ntr, samples)]))
+    # the network's permeability calibration, fitted on every 4th training box (like c_KC)
+    c_net = ws.fit_net_scale(net, boxes[:ntr:4], ks[:ntr:4], TAU, UBAR)
     _, f_step = net_flops(4, 32, side)
     train_flops = f_step * ntr * epochs
     test_mask, _ = sphere_pack(test_side, 8.0, 16.0, 0.35, seed=777)
@@ -919,9 +921,22 @@ def run_warmstart_leg(stream, samples=512, side=64, lbm_steps=8000, epochs=30, t
         ref = cv.run_to_residual(lat, Q, TAU, lag=1000, tol=1e-6, max_steps=ref_steps, sync=sync)
     t_ref = time.perf_counter() - t0
     abl = ws.ablation(Lattice, net, test_mask, Q, TAU, c_kc, ref["k"], stream=stream, sync=sync,
-                      max_steps=ref_steps, variant=variant)
-    k_net = ws.net_permeability(net, test_mask, Q, TAU)
-    k_kc = c_kc * ws.kc_features(test_mask)[2]
+                      max_steps=ref_steps, variant=variant, c_net=c_net)
+    # permeability estimates: the test pack and four more seeded 128^3 packs
+    est = []
+    for seed, m in [(777, test_mask)] + [(s, sphere_pack(128, 8.0, 16.0, 0.35, seed=s)[0]) for s in (901, 902, 903, 904)]:
+        Qm = UBAR * int((m[0] == 0).sum())
+        if seed == 777:
+            k_true = ref["k"]
+        else:
+            with Lattice(m, TAU, "mrt", "fp32", stream=stream) as lat:
+                lat.set_kernel(variant)
+                lat.set_flux_bc(Qm)
+                k_true = cv.run_to_residual(lat, Qm, TAU, lag=1000, tol=1e-6, max_steps=ref_steps, sync=sync)["k"]
+        k_n = ws.net_permeability(net, m, Qm, TAU, c_net=c_net)
+        k_c = c_kc * ws.kc_features(m)[2]
+        est.append({"side": m.shape[0], "seed": seed, "k_ref": k_true, "network_rel_err": (k_n - k_true) / k_true,
+                    "kozeny_carman_rel_err": (k_c - k_true) / k_true})
     clk = clocks.stop()
     conv = conv_roofline(stream)
     net.close()
@@ -947,14 +962,16 @@ def run_warmstart_leg(stream, samples=512, side=64, lbm_steps=8000, epochs=30, t
                      "starts": abl,
                      "starts_defined": {"cold": "rho 1, u 0", "kc_ramp": "rho: Kozeny-Carman Darcy ramp, u 0 (no "
                                         "network)", "net_velocity": "u: network, rho 1",
-                                        "net_pressure": "rho: network pressure profile, u 0",
+                                        "net_pressure": "rho: network pressure profile (calibrated by c_net), u 0",
                                         "net": "u and rho from the network"},
                      "change_vs_cold": {n: change(n, "cold") for n in ("kc_ramp", "net_velocity", "net_pressure",
                                                                        "net")},
                      "net_vs_kc_ramp": change("net", "kc_ramp"),
-                     "permeability_estimates": {"k_ref": ref["k"], "kozeny_carman": k_kc,
-                                                "kozeny_carman_rel_err": (k_kc - ref["k"]) / ref["k"],
-                                                "network": k_net, "network_rel_err": (k_net - ref["k"]) / ref["k"]}},
+                     "permeability_estimates": {
+                         "packs": est, "c_net": c_net, "c_kc": c_kc,
+                         "mean_abs_rel_err": {"network": float(np.mean([abs(e["network_rel_err"]) for e in est])),
+                                              "kozeny_carman": float(np.mean([abs(e["kozeny_carman_rel_err"])
+                                                                              for e in est]))}}},
             "conv_roofline": conv, "clocks": clk}
 
 
@@ -1042,7 +1059,7 @@ def main(argv=None):
                     help="run the learned warm-start leg alone instead of the benchmark (see --ws-test)")
     ap.add_argument("--ws-samples", type=int, default=512)
     ap.add_argument("--ws-lbm-steps", type=int, default=8000)
-    ap.add_argument("--ws-epochs", type=int, default=30)
+    ap.add_argument("--ws-epochs", type=int, default=40)
     ap.add_argument("--ws-test", type=int, default=256)
     ap.add_argument("--ws-ref-steps", type=int, default=300000)
     ap.add_argument("--two-fluid-case", action="store_true",

@@ -117,18 +117,31 @@ __device__ __forceinline__ uint4 pack8(const float* f) {
 // ---------------------------------------------- forward / data gradient ---
 template <int CIN, int COUT>
 struct ConvCfg {
-    static constexpr int AW = cmin(CIN, 64);            // channels per K chunk (one swizzle atom row)
+    static constexpr int AW = cmin(CIN, 64);            // channels per K chunk
     static constexpr int KSUB = CIN / AW;               // chunks per tap
-    static constexpr int NCHUNK = 27 * KSUB;
-    static constexpr uint32_t A_BYTES = kRows * AW * 2;
-    static constexpr uint32_t B_BYTES = COUT * AW * 2;
+    // FUSE (narrow outputs): one stage holds the 130 rows r0 - 1 .. r0 + 128 of
+    // one (dz, dy) row window, unswizzled as AW / 8 planes of 8-channel rows, and
+    // the weights of its three dx taps; the three taps' A operands are the same
+    // planes shifted by one row (16 bytes) each, so a tile loads its input rows
+    // 9 times instead of 27.  Wide outputs keep one tap per stage (128 rows,
+    // swizzled): their weights, not the activations, dominate the bytes.
+    static constexpr bool FUSE = COUT <= 64;
+    static constexpr int NITER = (FUSE ? 9 : 27) * KSUB;
+    static constexpr int HALO = kRows + 2;
+    static constexpr uint32_t PLANE = (HALO * 16 + 127) / 128 * 128;      // one 8-channel plane
+    static constexpr uint32_t A_BYTES = FUSE ? (AW / 8) * PLANE : kRows * AW * 2;
+    static constexpr uint32_t A_TX = FUSE ? (AW / 8) * HALO * 16 : A_BYTES;  // bytes the TMA delivers
+    static constexpr uint32_t B_TAP = COUT * AW * 2;
+    static constexpr uint32_t B_BYTES = (FUSE ? 3 : 1) * B_TAP;
     static constexpr uint32_t STAGE = A_BYTES + B_BYTES;
-    static constexpr int STAGES = 4 * STAGE <= 100 * 1024 ? cmin(8, (int)((100 * 1024) / STAGE))
-                                                          : cmin(6, (int)((200 * 1024) / STAGE));
-    static constexpr uint32_t SWZ = AW == 64 ? 2u : 4u;  // 128-byte or 64-byte swizzle
-    static constexpr uint32_t SBO = 8 * AW * 2;          // 8-row core-matrix group stride
+    static constexpr uint32_t STAGE_TX = A_TX + B_BYTES;
+    static constexpr int STAGES = 4 * STAGE <= 100 * 1024 ? cmin(8, (int)((96 * 1024) / STAGE))
+                                                          : cmin(6, (int)((196 * 1024) / STAGE));
+    static constexpr uint32_t A_REGION = (STAGES * A_BYTES + 1023) / 1024 * 1024;  // B stays 1024-aligned
+    static constexpr uint32_t SWZ = AW == 64 ? 2u : 4u;  // 128-byte or 64-byte swizzle (B; A when not FUSE)
+    static constexpr uint32_t SBO = 8 * AW * 2;          // 8-row core-matrix group stride (swizzled)
     static constexpr uint32_t COLS = COUT;
-    static constexpr size_t SMEM = 1024 + (size_t)STAGES * STAGE + 256;
+    static constexpr size_t SMEM = 1024 + (size_t)A_REGION + (size_t)STAGES * B_BYTES + 256;
 };
 
 struct ConvEpi {
@@ -152,7 +165,7 @@ k_conv(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorM
     extern __shared__ unsigned char smem_raw[];
     unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char* sA = base;
-    unsigned char* sB = base + K::STAGES * K::A_BYTES;
+    unsigned char* sB = base + K::A_REGION;
     uint64_t* full = (uint64_t*)(sB + K::STAGES * K::B_BYTES);
     uint64_t* empty = full + K::STAGES;
     uint64_t* accb = empty + K::STAGES;
@@ -176,27 +189,52 @@ k_conv(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorM
     const int xp = e.g.xp();
     if (warp == 0) {
         if (lane == 0) {
-            for (int j = 0; j < K::NCHUNK; ++j) {
+            for (int j = 0; j < K::NITER; ++j) {
                 const int s = j % K::STAGES, use = j / K::STAGES;
                 if (use > 0 && !tc::mbar_wait(&empty[s], (use - 1) & 1, e.err)) break;
-                const int t = j / K::KSUB, kc = j % K::KSUB;
-                tc::mbar_expect_tx(&full[s], K::STAGE);
-                tc::tma_load_2d(sA + s * K::A_BYTES, &mA, &full[s], kc * K::AW, (int)(r0 + tap_offset(t, plane, xp)));
-                tc::tma_load_2d(sB + s * K::B_BYTES, &mB, &full[s], t * CIN + kc * K::AW, 0);
+                const int w = j / K::KSUB, kc = j % K::KSUB;  // w: (dz, dy) window if FUSE, else the tap
+                tc::mbar_expect_tx(&full[s], K::STAGE_TX);
+                if constexpr (K::FUSE) {
+                    // rows of taps (w, dx = -1..1): r0 + off(3 w + 1) - 1 .. + 129
+                    const int row = (int)(r0 + tap_offset(3 * w + 1, plane, xp) - 1);
+#pragma unroll
+                    for (int g = 0; g < K::AW / 8; ++g)
+                        tc::tma_load_2d(sA + s * K::A_BYTES + g * K::PLANE, &mA, &full[s], kc * K::AW + g * 8, row);
+#pragma unroll
+                    for (int dx = 0; dx < 3; ++dx)
+                        tc::tma_load_2d(sB + s * K::B_BYTES + dx * K::B_TAP, &mB, &full[s],
+                                        (3 * w + dx) * CIN + kc * K::AW, 0);
+                } else {
+                    tc::tma_load_2d(sA + s * K::A_BYTES, &mA, &full[s], kc * K::AW,
+                                    (int)(r0 + tap_offset(w, plane, xp)));
+                    tc::tma_load_2d(sB + s * K::B_BYTES, &mB, &full[s], w * CIN + kc * K::AW, 0);
+                }
             }
         }
     } else if (warp == 1) {
         if (lane == 0) {
             constexpr uint32_t idesc = tc::idesc_bf16(kRows, COUT, false, false);
-            for (int j = 0; j < K::NCHUNK; ++j) {
+            for (int j = 0; j < K::NITER; ++j) {
                 const int s = j % K::STAGES, use = j / K::STAGES;
                 if (!tc::mbar_wait(&full[s], use & 1, e.err)) break;
                 tc::fence_after_sync();
                 const uint32_t a = tc::su32(sA + s * K::A_BYTES), b = tc::su32(sB + s * K::B_BYTES);
+                if constexpr (K::FUSE) {
+                    // unswizzled K-major A: 8-row core matrices 128 bytes apart (SBO),
+                    // 8-channel planes PLANE apart (LBO); tap dx starts dx rows in
 #pragma unroll
-                for (int k = 0; k < K::AW / 16; ++k)
-                    tc::mma_bf16(tmem, tc::smem_desc(a + k * 32, 16, K::SBO, K::SWZ),
-                                 tc::smem_desc(b + k * 32, 16, K::SBO, K::SWZ), idesc, (j | k) != 0);
+                    for (int dx = 0; dx < 3; ++dx)
+#pragma unroll
+                        for (int k = 0; k < K::AW / 16; ++k)
+                            tc::mma_bf16(tmem, tc::smem_desc(a + dx * 16 + k * 2 * K::PLANE, K::PLANE, 128, 0),
+                                         tc::smem_desc(b + dx * K::B_TAP + k * 32, 16, K::SBO, K::SWZ), idesc,
+                                         (j | dx | k) != 0);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < K::AW / 16; ++k)
+                        tc::mma_bf16(tmem, tc::smem_desc(a + k * 32, 16, K::SBO, K::SWZ),
+                                     tc::smem_desc(b + k * 32, 16, K::SBO, K::SWZ), idesc, (j | k) != 0);
+                }
                 tc::mma_commit(&empty[s]);
             }
             tc::mma_commit(accb);
@@ -647,7 +685,8 @@ cudaError_t make_map(CUtensorMap* m, const void* ptr, int C, int64_t rows, int b
     cuuint64_t strides[1] = {(cuuint64_t)C * 2};
     cuuint32_t box[2] = {(cuuint32_t)box_c, (cuuint32_t)box_r};
     cuuint32_t es[2] = {1, 1};
-    const CUtensorMapSwizzle sw = box_c * 2 == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
+    const CUtensorMapSwizzle sw = box_c * 2 == 128 ? CU_TENSOR_MAP_SWIZZLE_128B
+                                  : box_c * 2 == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_NONE;
     CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, es,
                           CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -660,7 +699,8 @@ cudaError_t conv_t(const bf16* in, const bf16* w, const ConvEpi& epi, cudaStream
     cudaError_t e0 = cudaFuncSetAttribute(k_conv<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)K::SMEM);
     if (e0 != cudaSuccess) return e0;
     CUtensorMap ma, mb;
-    cudaError_t e = make_map(&ma, in, CIN, epi.g.rows(), K::AW, kRows);
+    cudaError_t e = K::FUSE ? make_map(&ma, in, CIN, epi.g.rows(), 8, K::HALO)
+                            : make_map(&ma, in, CIN, epi.g.rows(), K::AW, kRows);
     if (e == cudaSuccess) e = make_map(&mb, w, 27 * CIN, COUT, K::AW, COUT);
     if (e != cudaSuccess) return e;
     const unsigned tiles = (unsigned)((epi.g.rows() + kRows - 1) / kRows);

@@ -20,7 +20,10 @@ much as those of the velocity.  Initial fields of a new geometry with flux Q:
   u = u_D * net_u(mask)                                       (network velocity)
   rho(z) = rho_out + (nu u_D / c_s^2) sum_{z' >= z} Hbar(z') / phi(z')
 with Hbar(z) the mean over the pore voxels of plane z of the predicted H
-(network pressure); or, without the network, the analytic ramp
+(network pressure), the drops divided by one constant c_net fitted on the
+training boxes like c_KC below (least squares in log k of the whole boxes'
+permeabilities against the network's); or, without the network, the analytic
+ramp
   rho(z) = rho_out + dp_est * (1 - z / (nz - 1)) / c_s^2,
   dp_est = nu u_D (nz - 1) / k_est,  k_est = c_KC phi^3 / (S^2 (1 - phi)^2)
 (Darcy with Kozeny-Carman), phi the porosity, S the pore-solid face count per
@@ -130,9 +133,10 @@ def fit_kc(masks, ks):
     return float(np.exp(np.mean(np.log(ks) - np.log(x))))
 
 
-def pressure_profile(G, mask, Q, tau, rho_out=1.0):
+def pressure_profile(G, mask, Q, tau, rho_out=1.0, c_net=1.0):
     """rho(z) from a predicted drop field (G_SCALE H): its plane means over the
-    pore voxels, divided by the plane porosity, summed from the outlet."""
+    pore voxels, divided by the plane porosity, summed from the outlet, and
+    divided by the calibration constant c_net."""
     nz, ny, nx = mask.shape
     nu = CS2 * (tau - 0.5)
     uD = Q / (nx * ny)
@@ -140,7 +144,7 @@ def pressure_profile(G, mask, Q, tau, rho_out=1.0):
     hbar = plane_means(np.asarray(G, dtype=np.float64), mask)[:-1] / G_SCALE
     gbar = np.where(phi > 0, hbar / np.maximum(phi, 1e-300), 0.0)
     drop = np.concatenate([np.cumsum(gbar[::-1])[::-1], [0.0]])  # sum over z' >= z of Gbar(z')
-    return rho_out + (nu * uD / CS2) * drop
+    return rho_out + (nu * uD / CS2) * drop / c_net
 
 
 def kc_profile(mask, Q, tau, c_kc, rho_out=1.0):
@@ -153,16 +157,16 @@ def kc_profile(mask, Q, tau, c_kc, rho_out=1.0):
     return rho_out + (dp / CS2) * (1.0 - np.arange(nz, dtype=np.float64) / (nz - 1))
 
 
-def initial_fields(net, mask, Q, tau, c_kc, velocity="net", pressure="net"):
+def initial_fields(net, mask, Q, tau, c_kc, velocity="net", pressure="net", c_net=1.0):
     """(rho, ux, uy, uz) float64 arrays for Lattice.set_fields.  velocity:
-    "net" (u = u_D * net_u) or "zero"; pressure: "net" (the network's profile),
-    "kc" (the Kozeny-Carman ramp) or "uniform" (rho = 1)."""
+    "net" (u = u_D * net_u) or "zero"; pressure: "net" (the network's profile,
+    calibrated by c_net), "kc" (the Kozeny-Carman ramp) or "uniform" (rho = 1)."""
     nz, ny, nx = mask.shape
     uD = Q / (nx * ny)
     y = net.predict(mask).astype(np.float64) if (velocity == "net" or pressure == "net") else None
     u = y[:3] * uD if velocity == "net" else np.zeros((3,) + mask.shape)
     if pressure == "net":
-        prof = pressure_profile(y[3], mask, Q, tau)
+        prof = pressure_profile(y[3], mask, Q, tau, c_net=c_net)
     elif pressure == "kc":
         prof = kc_profile(mask, Q, tau, c_kc)
     else:
@@ -171,11 +175,19 @@ def initial_fields(net, mask, Q, tau, c_kc, velocity="net", pressure="net"):
     return rho, u[0], u[1], u[2]
 
 
-def net_permeability(net, mask, Q, tau):
+def net_permeability(net, mask, Q, tau, c_net=1.0):
     """Darcy permeability implied by the network's pressure profile (the same
     definition the 0.1 % rule uses)."""
-    rho = pressure_profile(net.predict(mask)[3].astype(np.float64), mask, Q, tau)
+    rho = pressure_profile(net.predict(mask)[3].astype(np.float64), mask, Q, tau, c_net=c_net)
     return cv.permeability(Q, mask.shape, tau, rho[0], rho[-1])
+
+
+def fit_net_scale(net, boxes, ks, tau, u_mean):
+    """c_net: least squares in log k of the boxes' permeabilities against the
+    network's uncalibrated estimates (the analogue of fit_kc)."""
+    r = [np.log(k) - np.log(net_permeability(net, m, u_mean * int((m[0] == 0).sum()), tau))
+         for m, k in zip(boxes, ks)]
+    return float(np.exp(np.mean(r)))
 
 
 # start name -> (velocity, pressure) of initial_fields; "cold" sets nothing
@@ -184,7 +196,7 @@ STARTS = {"cold": None, "kc_ramp": ("zero", "kc"), "net_velocity": ("net", "unif
 
 
 def run_start(lattice_cls, net, mask, Q, tau, c_kc, k_ref, start, precision="fp32", stream=None, sync=None,
-              max_steps=400000, variant=0):
+              max_steps=400000, variant=0, c_net=1.0):
     """Steps and wall seconds to the 0.1 % rule (k within 1e-3 of k_ref for 10
     checks) from one of STARTS; the time of a warm start includes the network
     inference and the field upload."""
@@ -196,7 +208,7 @@ def run_start(lattice_cls, net, mask, Q, tau, c_kc, k_ref, start, precision="fp3
             if sync:
                 sync()
             t0 = time.perf_counter()
-            rho, ux, uy, uz = initial_fields(net, mask, Q, tau, c_kc, *STARTS[start])
+            rho, ux, uy, uz = initial_fields(net, mask, Q, tau, c_kc, *STARTS[start], c_net=c_net)
             lat.set_fields(rho, ux, uy, uz)
             if sync:
                 sync()
@@ -208,16 +220,16 @@ def run_start(lattice_cls, net, mask, Q, tau, c_kc, k_ref, start, precision="fp3
 
 
 def warm_vs_cold(lattice_cls, net, mask, Q, tau, c_kc, k_ref, precision="fp32", stream=None, sync=None,
-                 max_steps=400000, variant=0):
+                 max_steps=400000, variant=0, c_net=1.0):
     """The cold start and the full learned warm start (network velocity and pressure)."""
-    args = (precision, stream, sync, max_steps, variant)
+    args = (precision, stream, sync, max_steps, variant, c_net)
     return {"cold": run_start(lattice_cls, net, mask, Q, tau, c_kc, k_ref, "cold", *args),
             "warm": run_start(lattice_cls, net, mask, Q, tau, c_kc, k_ref, "net", *args)}
 
 
 def ablation(lattice_cls, net, mask, Q, tau, c_kc, k_ref, precision="fp32", stream=None, sync=None,
-             max_steps=400000, variant=0):
+             max_steps=400000, variant=0, c_net=1.0):
     """Every start of STARTS to the 0.1 % rule: what the network's velocity and
     pressure each add, and what it adds over the analytic Kozeny-Carman ramp."""
     return {name: run_start(lattice_cls, net, mask, Q, tau, c_kc, k_ref, name, precision, stream, sync,
-                            max_steps, variant) for name in STARTS}
+                            max_steps, variant, c_net) for name in STARTS}

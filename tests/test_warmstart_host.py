@@ -117,3 +117,42 @@ def test_kc_profile_is_the_darcy_ramp():
     # (rho_in - 1 is ~6e-8 here, so its FP64 rounding is ~2e-9 relative)
     from paper_1806_10589_gb300 import convergence as cv
     assert math.isclose(cv.permeability(Q, m.shape, tau, prof[0], prof[-1]), k_est, rel_tol=1e-7)
+
+
+def test_fit_net_scale_recovers_a_biased_network():
+    """A stand-in network whose pressure drops are twice the true ones implies
+    half the permeability; the calibration constant is then exactly 2, and the
+    calibrated estimate is the true permeability."""
+    from paper_1806_10589_gb300 import convergence as cv
+
+    tau, u_mean = 0.8, 1e-4
+    boxes, ks, fields = [], [], []
+    rng = np.random.default_rng(5)
+    for k in range(3):
+        m = (rng.random((8, 6, 6)) < 0.3).astype(np.uint8)
+        m[:, 0, 0] = 0
+        Q = u_mean * int((m[0] == 0).sum())
+        rho = 1.0 + 1e-4 * (7 - np.arange(8))[:, None, None] * (1 + 0.1 * rng.random(m.shape))
+        rho[-1] = 1.0
+        G = ws.drop_target(rho, m, Q, tau)
+        pbar = ws.plane_means(rho, m)
+        ks.append(cv.permeability(Q, m.shape, tau, pbar[0], 1.0))
+        boxes.append(m)
+        fields.append(np.nan_to_num(G))
+
+    class Biased:
+        def __init__(self):
+            self.k = 0
+
+        def predict(self, mask):
+            idx = [i for i, b in enumerate(boxes) if b is mask][0]
+            y = np.zeros((4,) + mask.shape, np.float32)
+            y[3] = 2.0 * fields[idx]
+            return y
+
+    net = Biased()
+    c = ws.fit_net_scale(net, boxes, ks, tau, u_mean)
+    assert math.isclose(c, 2.0, rel_tol=1e-6)
+    for m, k in zip(boxes, ks):
+        Q = u_mean * int((m[0] == 0).sum())
+        assert math.isclose(ws.net_permeability(net, m, Q, tau, c_net=c), k, rel_tol=1e-6)
