@@ -95,14 +95,18 @@ def strip_c_comments(src):
     return "".join(out)
 
 
-def kernel_sources_sha():
+BATCH_KERNEL_SOURCES = ("lbm_batch.cu", "lbm_device.cuh", "lbm_internal.h")
+PROFILE_BATCH = os.path.join(ROOT, "profiles", "k_batch_step_fp16_ensemble64.md")
+
+
+def kernel_sources_sha(sources=STEP_KERNEL_SOURCES):
     """Hash of the code (comments stripped, whitespace runs collapsed) of the
-    sources that define the single-lattice step kernel and its launch; other
-    modules of the library do not change it, and a comment or layout edit does
-    not invalidate a profile."""
+    sources that define a kernel and its launch (by default the single-lattice
+    step kernel); other modules of the library do not change it, and a comment
+    or layout edit does not invalidate a profile."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1806_10589_gb300", "csrc")
-    for f in STEP_KERNEL_SOURCES:
+    for f in sources:
         with open(os.path.join(csrc, f), encoding="utf-8") as fh:
             code = re.sub(r"\s+", " ", strip_c_comments(fh.read())).strip()
             h.update(f.encode() + b"\0" + code.encode())
@@ -136,11 +140,12 @@ def measured_bf16_peak():
     return 1900.0, "fallback 1.9 PFLOP/s"
 
 
-def profiled_traffic(sha, variant=0):
-    """dram bytes per launch of the step kernel from the committed ncu summary,
-    if it was taken on the current kernel sources (else None)."""
+def profiled_traffic(sha, variant=0, path=None):
+    """dram bytes per launch of the step kernel (or of the kernel whose summary
+    is `path`) from the committed ncu summary, if it was taken on the current
+    kernel sources (else None)."""
     try:
-        txt = open(PROFILE_TRAFFIC[variant]).read()
+        txt = open(path or PROFILE_TRAFFIC[variant]).read()
     except (OSError, KeyError):
         return None
     m_sha = re.search(r"kernel_sources_sha:\s*([0-9a-f]+)", txt)
@@ -539,6 +544,8 @@ def run_ensemble(stream, prec="fp16dev", steps=2000, warmup=64, steady_steps=Tru
             "ms_per_step": round(ms / steps, 5),
             "roofline": {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(ach / peak, 4),
+                         "traffic": profiled_traffic(kernel_sources_sha(BATCH_KERNEL_SOURCES), path=PROFILE_BATCH)
+                         if best in (0, 1) else None,
                          "kernel": {2: "k_batch_persistent", 3: "k_batch_persistent", 4: "k_batch_aa", 5: "k_batch_aa"}.get(best, "k_batch_step"),
                          "kernel_ms": round(k_ms, 5), "bytes_per_unit": 2 * 19 * s},
             "autotune": {"chosen": BATCH_CONFIGS[best],
