@@ -120,18 +120,21 @@ struct ConvCfg {
     static constexpr int AW = cmin(CIN, 64);            // channels per K chunk
     static constexpr int KSUB = CIN / AW;               // chunks per tap
     // FUSE (narrow outputs): one stage holds the 130 rows r0 - 1 .. r0 + 128 of
-    // one (dz, dy) row window, unswizzled as AW / 8 planes of 8-channel rows, and
-    // the weights of its three dx taps; the three taps' A operands are the same
-    // planes shifted by one row (16 bytes) each, so a tile loads its input rows
-    // 9 times instead of 27 (measured on the 32 -> 32 layer, 8 x 64^3 voxels:
-    // 0.390 against 0.474 ms per launch).  Wide outputs keep one tap per stage
-    // (128 rows, swizzled): their weights, not the activations, dominate the bytes.
+    // one (dz, dy) row window (one swizzled TMA box) and the weights of its three
+    // dx taps; the three taps' A operands are the same window started one row
+    // (AW * 2 bytes) apart, so a tile loads its input rows 9 times instead of 27.
+    // Wide outputs keep one tap per stage (128 rows): their weights, not the
+    // activations, dominate the bytes.  Measured on the 32 -> 32 layer, 8 x 64^3
+    // voxels, per forward launch: 0.474 ms one tap per stage, 0.390 ms with the
+    // window as four unswizzled 8-channel planes, 0.318 ms as one swizzled box;
+    // slower: a persistent form with two TMEM accumulators (0.416 ms), weights
+    // kept resident in shared memory (0.557 ms one tile per CTA, 0.458 ms
+    // persistent).
     static constexpr bool FUSE = COUT <= 64;
     static constexpr int NITER = (FUSE ? 9 : 27) * KSUB;
     static constexpr int HALO = kRows + 2;
-    static constexpr uint32_t PLANE = (HALO * 16 + 127) / 128 * 128;      // one 8-channel plane
-    static constexpr uint32_t A_BYTES = FUSE ? (AW / 8) * PLANE : kRows * AW * 2;
-    static constexpr uint32_t A_TX = FUSE ? (AW / 8) * HALO * 16 : A_BYTES;  // bytes the TMA delivers
+    static constexpr uint32_t A_BYTES = FUSE ? (HALO * AW * 2 + 1023) / 1024 * 1024 : kRows * AW * 2;
+    static constexpr uint32_t A_TX = FUSE ? HALO * AW * 2 : A_BYTES;  // bytes the TMA delivers
     static constexpr uint32_t B_TAP = COUT * AW * 2;
     static constexpr uint32_t B_BYTES = (FUSE ? 3 : 1) * B_TAP;
     static constexpr uint32_t STAGE = A_BYTES + B_BYTES;
@@ -198,9 +201,7 @@ k_conv(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorM
                 if constexpr (K::FUSE) {
                     // rows of taps (w, dx = -1..1): r0 + off(3 w + 1) - 1 .. + 129
                     const int row = (int)(r0 + tap_offset(3 * w + 1, plane, xp) - 1);
-#pragma unroll
-                    for (int g = 0; g < K::AW / 8; ++g)
-                        tc::tma_load_2d(sA + s * K::A_BYTES + g * K::PLANE, &mA, &full[s], kc * K::AW + g * 8, row);
+                    tc::tma_load_2d(sA + s * K::A_BYTES, &mA, &full[s], kc * K::AW, row);
 #pragma unroll
                     for (int dx = 0; dx < 3; ++dx)
                         tc::tma_load_2d(sB + s * K::B_BYTES + dx * K::B_TAP, &mB, &full[s],
@@ -221,13 +222,13 @@ k_conv(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorM
                 tc::fence_after_sync();
                 const uint32_t a = tc::su32(sA + s * K::A_BYTES), b = tc::su32(sB + s * K::B_BYTES);
                 if constexpr (K::FUSE) {
-                    // unswizzled K-major A: 8-row core matrices 128 bytes apart (SBO),
-                    // 8-channel planes PLANE apart (LBO); tap dx starts dx rows in
+                    // the swizzled window started dx rows in (the swizzle follows the
+                    // absolute shared-memory address, so a row offset needs no base offset)
 #pragma unroll
                     for (int dx = 0; dx < 3; ++dx)
 #pragma unroll
                         for (int k = 0; k < K::AW / 16; ++k)
-                            tc::mma_bf16(tmem, tc::smem_desc(a + dx * 16 + k * 2 * K::PLANE, K::PLANE, 128, 0),
+                            tc::mma_bf16(tmem, tc::smem_desc(a + dx * K::AW * 2 + k * 32, 16, K::SBO, K::SWZ),
                                          tc::smem_desc(b + dx * K::B_TAP + k * 32, 16, K::SBO, K::SWZ), idesc,
                                          (j | dx | k) != 0);
                 } else {
@@ -700,8 +701,7 @@ cudaError_t conv_t(const bf16* in, const bf16* w, const ConvEpi& epi, cudaStream
     cudaError_t e0 = cudaFuncSetAttribute(k_conv<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)K::SMEM);
     if (e0 != cudaSuccess) return e0;
     CUtensorMap ma, mb;
-    cudaError_t e = K::FUSE ? make_map(&ma, in, CIN, epi.g.rows(), 8, K::HALO)
-                            : make_map(&ma, in, CIN, epi.g.rows(), K::AW, kRows);
+    cudaError_t e = make_map(&ma, in, CIN, epi.g.rows(), K::AW, K::FUSE ? K::HALO : kRows);
     if (e == cudaSuccess) e = make_map(&mb, w, 27 * CIN, COUT, K::AW, COUT);
     if (e != cudaSuccess) return e;
     const unsigned tiles = (unsigned)((epi.g.rows() + kRows - 1) / kRows);
