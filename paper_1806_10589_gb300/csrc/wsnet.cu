@@ -126,7 +126,8 @@ struct ConvCfg {
     // Wide outputs keep one tap per stage (128 rows): their weights, not the
     // activations, dominate the bytes.  Measured on the 32 -> 32 layer, 8 x 64^3
     // voxels, per forward launch: 0.474 ms one tap per stage, 0.390 ms with the
-    // window as four unswizzled 8-channel planes, 0.318 ms as one swizzled box;
+    // window as four unswizzled 8-channel planes, 0.318 ms as one swizzled box,
+    // 0.311 ms with the three taps' weights as one box of the tap-major copy;
     // slower: a persistent form with two TMEM accumulators (0.416 ms), weights
     // kept resident in shared memory (0.557 ms one tile per CTA, 0.458 ms
     // persistent).
@@ -202,10 +203,8 @@ k_conv(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorM
                     // rows of taps (w, dx = -1..1): r0 + off(3 w + 1) - 1 .. + 129
                     const int row = (int)(r0 + tap_offset(3 * w + 1, plane, xp) - 1);
                     tc::tma_load_2d(sA + s * K::A_BYTES, &mA, &full[s], kc * K::AW, row);
-#pragma unroll
-                    for (int dx = 0; dx < 3; ++dx)
-                        tc::tma_load_2d(sB + s * K::B_BYTES + dx * K::B_TAP, &mB, &full[s],
-                                        (3 * w + dx) * CIN + kc * K::AW, 0);
+                    // taps 3 w .. 3 w + 2 of the tap-major weights: one box of 3 COUT rows
+                    tc::tma_load_2d(sB + s * K::B_BYTES, &mB, &full[s], kc * K::AW, 3 * w * COUT);
                 } else {
                     tc::tma_load_2d(sA + s * K::A_BYTES, &mA, &full[s], kc * K::AW,
                                     (int)(r0 + tap_offset(w, plane, xp)));
@@ -632,6 +631,7 @@ struct LayerDesc {
     int cout, cin, cout_p, cin_p;
     int64_t woff, boff;      // into the FP32 parameter vector
     int64_t wf, wb, bp;      // into the BF16 weight store / padded bias store
+    int64_t wft, wbt;        // the same weights tap-major: [t][cout][cin] and [t][cin][cout]
 };
 
 // BF16 forward weights wf[co][t][ci], data-gradient weights wb[ci][t][co] =
@@ -643,9 +643,11 @@ __global__ void k_pack(const float* __restrict__ p, const LayerDesc* __restrict_
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
         const int ci = (int)(k % d.cin_p), t = (int)((k / d.cin_p) % 27), co = (int)(k / (27 * d.cin_p));
         const bool real = co < d.cout && ci < d.cin;
-        wst[d.wf + k] = __float2bfloat16_rn(real ? p[d.woff + ((int64_t)co * 27 + t) * d.cin + ci] : 0.f);
-        wst[d.wb + ((int64_t)ci * 27 + (26 - t)) * d.cout_p + co] =
-            __float2bfloat16_rn(real ? p[d.woff + ((int64_t)co * 27 + t) * d.cin + ci] : 0.f);
+        const bf16 v = __float2bfloat16_rn(real ? p[d.woff + ((int64_t)co * 27 + t) * d.cin + ci] : 0.f);
+        wst[d.wf + k] = v;
+        wst[d.wb + ((int64_t)ci * 27 + (26 - t)) * d.cout_p + co] = v;
+        wst[d.wft + ((int64_t)t * d.cout_p + co) * d.cin_p + ci] = v;
+        wst[d.wbt + ((int64_t)(26 - t) * d.cin_p + ci) * d.cout_p + co] = v;
     }
     if (blockIdx.x == 0)
         for (int c = threadIdx.x; c < d.cout_p; c += blockDim.x) bst[d.bp + c] = c < d.cout ? p[d.boff + c] : 0.f;
@@ -695,14 +697,17 @@ cudaError_t make_map(CUtensorMap* m, const void* ptr, int C, int64_t rows, int b
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+// w: weights [COUT][27][CIN]; wt: the same tap-major, [27][COUT][CIN] (the
+// fused layers load the three dx taps of a tap row as one box from it)
 template <int CIN, int COUT>
-cudaError_t conv_t(const bf16* in, const bf16* w, const ConvEpi& epi, cudaStream_t st) {
+cudaError_t conv_t(const bf16* in, const bf16* w, const bf16* wt, const ConvEpi& epi, cudaStream_t st) {
     using K = ConvCfg<CIN, COUT>;
     cudaError_t e0 = cudaFuncSetAttribute(k_conv<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)K::SMEM);
     if (e0 != cudaSuccess) return e0;
     CUtensorMap ma, mb;
     cudaError_t e = make_map(&ma, in, CIN, epi.g.rows(), K::AW, K::FUSE ? K::HALO : kRows);
-    if (e == cudaSuccess) e = make_map(&mb, w, 27 * CIN, COUT, K::AW, COUT);
+    if (e == cudaSuccess)
+        e = K::FUSE ? make_map(&mb, wt, CIN, 27 * COUT, K::AW, 3 * COUT) : make_map(&mb, w, 27 * CIN, COUT, K::AW, COUT);
     if (e != cudaSuccess) return e;
     const unsigned tiles = (unsigned)((epi.g.rows() + kRows - 1) / kRows);
     k_conv<CIN, COUT><<<tiles, kThreads, K::SMEM, st>>>(ma, mb, epi);
@@ -748,8 +753,9 @@ cudaError_t wgrad_t(const bf16* act, const bf16* gout, const WgArgs& a0, cudaStr
         default: return cudaErrorInvalidValue;                               \
     }
 
-cudaError_t conv(int cin, int cout, const bf16* in, const bf16* w, const ConvEpi& epi, cudaStream_t st) {
-    WS_DISPATCH(conv_t, cin, cout, in, w, epi, st)
+cudaError_t conv(int cin, int cout, const bf16* in, const bf16* w, const bf16* wt, const ConvEpi& epi,
+                 cudaStream_t st) {
+    WS_DISPATCH(conv_t, cin, cout, in, w, wt, epi, st)
 }
 cudaError_t wgrad(int cin, int cout, const bf16* act, const bf16* gout, const WgArgs& a, cudaStream_t st, int n_sm) {
     WS_DISPATCH(wgrad_t, cin, cout, act, gout, a, st, n_sm)
@@ -913,7 +919,7 @@ int fwd_layer(lbm_wsnet* n, int k, const bf16* in, int l, bool relu, bf16* out, 
     e.xin = xin;
     e.err = n->d_err;
     e.g = level_geo(n, l);
-    WS_CUDA(n, wsn::conv(d.cin_p, d.cout_p, in, n->wst + d.wf, e, n->stream));
+    WS_CUDA(n, wsn::conv(d.cin_p, d.cout_p, in, n->wst + d.wf, n->wst + d.wft, e, n->stream));
     return LBM_OK;
 }
 
@@ -926,7 +932,7 @@ int bwd_data(lbm_wsnet* n, int k, const bf16* gout, int l, bf16* out, const bf16
     e.out_mask = out_mask;
     e.err = n->d_err;
     e.g = level_geo(n, l);
-    WS_CUDA(n, wsn::conv(d.cout_p, d.cin_p, gout, n->wst + d.wb, e, n->stream));
+    WS_CUDA(n, wsn::conv(d.cout_p, d.cin_p, gout, n->wst + d.wb, n->wst + d.wbt, e, n->stream));
     return LBM_OK;
 }
 
@@ -1157,6 +1163,10 @@ int lbm_wsnet_create(int levels, int base, lbm_wsnet** out) {
         w += (int64_t)d.cout_p * 27 * d.cin_p;
         d.wb = w;
         w += (int64_t)d.cout_p * 27 * d.cin_p;
+        d.wft = w;
+        w += (int64_t)d.cout_p * 27 * d.cin_p;
+        d.wbt = w;
+        w += (int64_t)d.cout_p * 27 * d.cin_p;
         d.bp = b;
         b += d.cout_p;
         n->L.push_back(d);
@@ -1365,16 +1375,26 @@ int conv_call(int op, const void* in, const void* aux, const void* w, const floa
     int* d_err = nullptr;
     if (cudaMalloc(&d_err, sizeof(int)) != cudaSuccess) return LBM_ENOMEM;
     cudaError_t e = cudaMemsetAsync(d_err, 0, sizeof(int), st);
-    bf16* wb = nullptr;
-    if (e == cudaSuccess && op == 1) {
-        // data gradient: flip and transpose the weights into [cin][27][cout]
-        std::vector<uint16_t> hw((size_t)cout * 27 * cin), hb(hw.size());
-        e = cudaMemcpyAsync(hw.data(), w, hw.size() * 2, cudaMemcpyDeviceToHost, st);
+    // the layouts the convolution kernel reads: forward [cout][27][cin] and
+    // [27][cout][cin]; data gradient (flipped taps) [cin][27][cout] and [27][cin][cout]
+    bf16* wb = nullptr;  // two arrays: wb and wb + n
+    const size_t nw = (size_t)cout * 27 * cin;
+    if (e == cudaSuccess && op < 2) {
+        std::vector<uint16_t> hw(nw), hb(2 * nw);
+        e = cudaMemcpyAsync(hw.data(), w, nw * 2, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         for (int co = 0; co < cout && e == cudaSuccess; ++co)
             for (int t = 0; t < 27; ++t)
-                for (int ci = 0; ci < cin; ++ci)
-                    hb[((size_t)ci * 27 + (26 - t)) * cout + co] = hw[((size_t)co * 27 + t) * cin + ci];
+                for (int ci = 0; ci < cin; ++ci) {
+                    const uint16_t v = hw[((size_t)co * 27 + t) * cin + ci];
+                    if (op == 0) {
+                        hb[((size_t)co * 27 + t) * cin + ci] = v;
+                        hb[nw + ((size_t)t * cout + co) * cin + ci] = v;
+                    } else {
+                        hb[((size_t)ci * 27 + (26 - t)) * cout + co] = v;
+                        hb[nw + ((size_t)(26 - t) * cin + ci) * cout + co] = v;
+                    }
+                }
         if (e == cudaSuccess) e = cudaMalloc(&wb, hb.size() * 2);
         if (e == cudaSuccess) e = cudaMemcpyAsync(wb, hb.data(), hb.size() * 2, cudaMemcpyHostToDevice, st);
     }
@@ -1393,13 +1413,13 @@ int conv_call(int op, const void* in, const void* aux, const void* w, const floa
             ep.out = (bf16*)out;
             ep.err = d_err;
             ep.g = g;
-            e = wsn::conv(cin, cout, (const bf16*)in, (const bf16*)w, ep, st);
+            e = wsn::conv(cin, cout, (const bf16*)in, wb, wb + nw, ep, st);
         } else if (op == 1) {
             wsn::ConvEpi ep{};
             ep.out = (bf16*)out;
             ep.err = d_err;
             ep.g = g;
-            e = wsn::conv(cout, cin, (const bf16*)in, wb, ep, st);
+            e = wsn::conv(cout, cin, (const bf16*)in, wb, wb + nw, ep, st);
         } else {
             wsn::WgArgs a{};
             a.gw = (float*)out;
