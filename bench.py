@@ -97,6 +97,8 @@ def strip_c_comments(src):
 
 BATCH_KERNEL_SOURCES = ("lbm_batch.cu", "lbm_device.cuh", "lbm_internal.h")
 PROFILE_BATCH = os.path.join(ROOT, "profiles", "k_batch_step_fp16_ensemble64.md")
+CONV_KERNEL_SOURCES = ("wsnet.cu", "tc_util.cuh")
+PROFILE_CONV = os.path.join(ROOT, "profiles", "k_conv_wgrad_bf16_32x32.md")
 
 
 def kernel_sources_sha(sources=STEP_KERNEL_SOURCES):
@@ -870,11 +872,11 @@ def conv_roofline(stream, side=64, batch=8, reps=20):
     peak, kind = measured_bf16_peak()
     per = {k: {"ms": round(v, 5), "achieved": round(flops / (v * 1e-3) / 1e12, 1),
                "frac": round(flops / (v * 1e-3) / 1e12 / peak, 4)} for k, v in ms.items()}
-    top = min(ms, key=ms.get)
     return {"bound": "tensor", "unit": "TFLOP/s", "peak": peak, "peak_source": kind,
             "shape": "3x3x3 conv 32 -> 32 channels, %d x %d^3 voxels (BF16, FP32 accumulate)" % (batch, side),
-            "flops_per_launch": flops, "per_kernel": per, "achieved": per[top]["achieved"],
-            "frac": per[top]["frac"], "kernel": "k_conv<32,32> / k_wgrad<32,32>", "traffic": None}
+            "flops_per_launch": flops, "per_kernel": per, "achieved": per["forward"]["achieved"],
+            "frac": per["forward"]["frac"], "kernel": "k_conv<32,32> (forward)",
+            "traffic": profiled_traffic(kernel_sources_sha(CONV_KERNEL_SOURCES), path=PROFILE_CONV)}
 
 
 def run_warmstart_leg(stream, samples=512, side=64, lbm_steps=8000, epochs=40, test_side=256, variant=3,

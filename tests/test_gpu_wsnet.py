@@ -307,3 +307,36 @@ def test_adam_steps_match_the_published_update(torch):
     assert np.abs(p2 - want2)[big].max() <= 2e-3 * lr
     # the first step moves every parameter by lr |g| / (|g| + eps) <= lr
     assert np.abs(p1 - p0).max() <= lr * (1 + 1e-3)
+
+
+def test_exact_pressure_start_beats_cold(torch):
+    """What the network's pressure output buys when it is exact: a stand-in
+    network that returns the pack's own steady plane drops (and no velocity)
+    starts the run at the right pressure, and the run meets the 0.1 % rule in
+    well under half the steps of a cold start.  The trained network's gain is
+    measured by the benchmark's warm-start leg."""
+    from lbm_inputs import sphere_pack
+    from paper_1806_10589_gb300 import Lattice, convergence as cv, warmstart as ws
+
+    st = torch.cuda.current_stream()
+    # long in z, so that the pressure (the slow mode, time ~ length^2) sets the pace
+    m = sphere_pack((32, 32, 128), 5.0, 8.0, 0.4, seed=999, cache=False)[0]
+    assert m.shape == (128, 32, 32)
+    Q, tau = 1e-4 * int((m[0] == 0).sum()), 0.8
+    with Lattice(m, tau, "mrt", "fp32", stream=st) as lat:
+        lat.set_flux_bc(Q)
+        ref = cv.run_to_residual(lat, Q, tau, lag=1000, tol=1e-6, max_steps=100000)
+        rho, _, _, _ = lat.fields()
+    G = np.nan_to_num(ws.drop_target(rho, m, Q, tau)).astype(np.float32)
+
+    class Exact:
+        def predict(self, mask):
+            y = np.zeros((4,) + mask.shape, np.float32)
+            y[3] = G
+            return y
+
+    cold = ws.run_start(Lattice, None, m, Q, tau, 1.0, ref["k"], "cold", stream=st, max_steps=100000)
+    warm = ws.run_start(Lattice, Exact(), m, Q, tau, 1.0, ref["k"], "net_pressure", stream=st, max_steps=100000)
+    assert cold["reached"] and warm["reached"], (cold, warm)
+    assert warm["steps"] <= 0.5 * cold["steps"], (warm["steps"], cold["steps"])
+    assert abs(warm["k"] - ref["k"]) <= 1e-3 * ref["k"]
