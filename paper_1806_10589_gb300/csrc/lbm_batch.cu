@@ -56,6 +56,14 @@ struct Member {
     uint32_t sr_seed[2];        // stochastic-rounding seed of the step reading buffer c (16-bit)
 };
 
+// LBM_BATCH16_PAIR_SCATTER: as LBM_AA16_PAIR_SCATTER, for the ensemble's
+// gather-scatter step.  Measured on the 64-pack FP16-dev ensemble, the
+// opposite order from the single lattice: the AA step pair takes 1.264 ms with
+// one conversion per pair and 1.316 ms with one per value.
+#ifndef LBM_BATCH16_PAIR_SCATTER
+#define LBM_BATCH16_PAIR_SCATTER 1
+#endif
+
 template <int... Qs, class F>
 __device__ __forceinline__ void for_q(std::integer_sequence<int, Qs...>, F&& f) {
     (f(std::integral_constant<int, Qs>{}), ...);
@@ -208,9 +216,9 @@ __device__ __forceinline__ void batch_tile_step(const typename S::T* fin, typena
             close_outlet(d, outlet_known(d) - M(m.drho_out));
         }
         collide(d, sp, sm);
-        for_q(AllQ{}, [&](auto qc) {
+        encode_node<S>(d, seed, i, [&](auto) { return r_own; }, [&](auto qc, typename S::T v) {
             constexpr int Q = decltype(qc)::value;
-            fout[(int64_t)Q * ns + i] = S::template enc_sr<Q>(d[Q], r_own, sr_key<S>(seed, i, Q));
+            fout[(int64_t)Q * ns + i] = v;
         });
         if (il < m.a_01) part = next_inlet_part_b<S>(d, grid, m, p, il, r_own, seed, i);
     }
@@ -400,17 +408,40 @@ k_batch_aa(const Rows<typename S::T> F, int slot, const uint32_t* __restrict__ v
         if constexpr (ODD) {
             const int64_t ps = __ldg(vox + j);
             F.row[0][j] = S::template enc_sr<0>(d[0], r_own, sr_key<S>(seed, i, 0));
-            for_q(std::make_integer_sequence<int, 18>{}, [&](auto qc) {
-                constexpr int Q = decltype(qc)::value + 1;
-                const int dst = __ldg(grid + ps + m.goff[opp(Q)]);  // x + xi_Q is the pull source of opp(Q)
-                const uint32_t key = sr_key<S>(seed, i, Q);
-                if (dst >= 0) F.row[Q][dst] = S::template enc_sr<Q>(d[Q], r_own + M(cz(Q)) * g, key);
-                else F.row[opp(Q)][j] = S::template enc_sr<Q>(d[Q], r_own, key);
-            });
+            if constexpr (S::kRef && !LBM_BATCH16_PAIR_SCATTER) {
+                for_q(std::make_integer_sequence<int, 18>{}, [&](auto qc) {
+                    constexpr int Q = decltype(qc)::value + 1;
+                    const int dst = __ldg(grid + ps + m.goff[opp(Q)]);  // x + xi_Q is the pull source of opp(Q)
+                    const uint32_t key = sr_key<S>(seed, i, Q);
+                    if (dst >= 0) F.row[Q][dst] = S::template enc_sr<Q>(d[Q], r_own + M(cz(Q)) * g, key);
+                    else F.row[opp(Q)][j] = S::template enc_sr<Q>(d[Q], r_own, key);
+                });
+            } else if constexpr (S::kRef) {
+                // per opposite pair one stochastic conversion, then one store per value
+                for_q(std::make_integer_sequence<int, 9>{}, [&](auto pc) {
+                    constexpr int Q = 2 * decltype(pc)::value + 1;
+                    const int dq = __ldg(grid + ps + m.goff[Q + 1]);   // x + xi_Q is the pull source of Q + 1
+                    const int dq1 = __ldg(grid + ps + m.goff[Q]);      // and x - xi_Q that of Q
+                    const uint32_t h = S::template enc_sr2<Q>(d[Q], dq >= 0 ? r_own + M(cz(Q)) * g : r_own, d[Q + 1],
+                                                              dq1 >= 0 ? r_own - M(cz(Q)) * g : r_own,
+                                                              sr_key<S>(seed, i, Q));
+                    if (dq >= 0) F.row[Q][dq] = S::half_of(h, true);
+                    else F.row[Q + 1][j] = S::half_of(h, true);
+                    if (dq1 >= 0) F.row[Q + 1][dq1] = S::half_of(h, false);
+                    else F.row[Q][j] = S::half_of(h, false);
+                });
+            } else {
+                for_q(std::make_integer_sequence<int, 18>{}, [&](auto qc) {
+                    constexpr int Q = decltype(qc)::value + 1;
+                    const int dst = __ldg(grid + ps + m.goff[opp(Q)]);  // x + xi_Q is the pull source of opp(Q)
+                    if (dst >= 0) F.row[Q][dst] = d[Q];
+                    else F.row[opp(Q)][j] = d[Q];
+                });
+            }
         } else {
-            for_q(AllQ{}, [&](auto qc) {
+            encode_node<S>(d, seed, i, [&](auto) { return r_own; }, [&](auto qc, typename S::T v) {
                 constexpr int Q = decltype(qc)::value;
-                F.row[opp(Q)][j] = S::template enc_sr<Q>(d[Q], r_own, sr_key<S>(seed, i, Q));
+                F.row[opp(Q)][j] = v;
             });
         }
         if (il < m.a_01) {

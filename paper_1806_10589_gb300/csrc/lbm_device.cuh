@@ -11,6 +11,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <utility>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -58,9 +59,22 @@ constexpr int ZOUT = -2;
 // lower neighbour in units of the last place, so the rounding error has zero
 // mean.  Round-to-nearest would repeat the same error every step once the flow
 // is steady and bias the steady state.  The random bits come from a
-// counter-based hash of (step seed, node, direction), so a run is reproducible.
-// Format conversions (encode, refresh) round to nearest.
+// counter-based hash of (step seed, node, direction pair), so a run is
+// reproducible.  Format conversions (encode, refresh) round to nearest.
+//
+// The rounding is the conversion instruction cvt.rs.{f16x2,bf16x2}.f32 (PTX ISA
+// 8.7, sm_100a and later): it converts two FP32 values into one packed pair,
+// adding the bits of its 32-bit rbits operand to the discarded low bits of each
+// magnitude and truncating.  Lane layout (measured on sm_103a with values
+// placed exactly below a rounding boundary, one rbits bit set at a time): the
+// value in the upper half takes rbits bits 16-28 (FP16: 13 discarded bits) or
+// 16-31 (BF16: 16), the value in the lower half bits 0-12 or 0-15.  So one
+// 32-bit key serves a pair of opposite directions (q odd, q + 1): q odd and the
+// rest direction 0 take the upper half, q even the lower half; enc_sr2 rounds
+// both values of a pair with one instruction.
 constexpr float DEV_SCALE = 1024.0f;
+// Half of the packed stochastic conversion that direction q uses.
+__host__ __device__ constexpr bool sr_upper(int q) { return q == 0 || (q & 1); }
 
 // 32-bit integer hash: the "lowbias32" finaliser published by C. Wellons
 // (xor-shift / multiply rounds).
@@ -103,11 +117,23 @@ struct StoreF16 {
     template <int Q> __device__ static T enc(M v, M r) {
         return __float2half_rn(fmaf(v, float(1024.0 / wq(Q)), -1024.0f * r));
     }
-    // FP32 keeps 13 more fraction bits than FP16: adding 13 random bits to the
-    // magnitude and truncating rounds stochastically (FP16 normal range).
+    // stochastic rounding of the values of Q (upper half) and Q + 1 (lower half)
+    __device__ static uint32_t cvt_rs(float hi, float lo, uint32_t u) {
+        uint32_t d;
+        asm("cvt.rs.satfinite.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(u));
+        return d;
+    }
+    __device__ static T half_of(uint32_t d, bool upper) {
+        return __ushort_as_half((unsigned short)(upper ? d >> 16 : d & 0xFFFFu));
+    }
+    template <int Q> __device__ static float scaled(M v, M r) { return fmaf(v, float(1024.0 / wq(Q)), -1024.0f * r); }
     template <int Q> __device__ static T enc_sr(M v, M r, uint32_t u) {
-        const float x = fmaf(v, float(1024.0 / wq(Q)), -1024.0f * r);
-        return __float2half_rz(__uint_as_float(__float_as_uint(x) + (u >> 19)));
+        constexpr bool up = sr_upper(Q);
+        return half_of(up ? cvt_rs(scaled<Q>(v, r), 0.0f, u) : cvt_rs(0.0f, scaled<Q>(v, r), u), up);
+    }
+    template <int Q> __device__ static uint32_t enc_sr2(M v, M r, M v1, M r1, uint32_t u) {
+        static_assert(Q & 1, "a pair starts at an odd direction");
+        return cvt_rs(scaled<Q>(v, r), scaled<Q + 1>(v1, r1), u);
     }
 };
 struct StoreBF16 {
@@ -120,21 +146,66 @@ struct StoreBF16 {
     template <int Q> __device__ static T enc(M v, M r) {
         return __float2bfloat16_rn(fmaf(v, float(1024.0 / wq(Q)), -1024.0f * r));
     }
-    // BF16 is the upper half of FP32: add 16 random bits, then truncate.
+    __device__ static uint32_t cvt_rs(float hi, float lo, uint32_t u) {
+        uint32_t d;
+        asm("cvt.rs.satfinite.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(u));
+        return d;
+    }
+    __device__ static T half_of(uint32_t d, bool upper) {
+        return __ushort_as_bfloat16((unsigned short)(upper ? d >> 16 : d & 0xFFFFu));
+    }
+    template <int Q> __device__ static float scaled(M v, M r) { return fmaf(v, float(1024.0 / wq(Q)), -1024.0f * r); }
     template <int Q> __device__ static T enc_sr(M v, M r, uint32_t u) {
-        const float x = fmaf(v, float(1024.0 / wq(Q)), -1024.0f * r);
-        return __float2bfloat16_rz(__uint_as_float(__float_as_uint(x) + (u >> 16)));
+        constexpr bool up = sr_upper(Q);
+        return half_of(up ? cvt_rs(scaled<Q>(v, r), 0.0f, u) : cvt_rs(0.0f, scaled<Q>(v, r), u), up);
+    }
+    template <int Q> __device__ static uint32_t enc_sr2(M v, M r, M v1, M r1, uint32_t u) {
+        static_assert(Q & 1, "a pair starts at an odd direction");
+        return cvt_rs(scaled<Q>(v, r), scaled<Q + 1>(v1, r1), u);
     }
 };
 
 // Random bits of the stochastic rounding of value (node i, direction q) in the
 // step with seed `seed` (no work for the formats that store exactly): one hash
 // per node (the same call for every q, computed once), then a Weyl step per
-// direction mixed by one multiply; the codecs use the high bits of the product.
+// direction pair (q + 1) / 2 mixed by one multiply.  The pair's two values take
+// disjoint bit fields of the product (see the codecs), so they are rounded
+// independently.
 template <class S>
 __device__ __forceinline__ uint32_t sr_key(uint32_t seed, int64_t i, int q) {
-    if constexpr (S::kRef) return (sr_hash(seed ^ (uint32_t)i) + (uint32_t)q * 0x9E3779B9U) * 0x2C1B3C6DU;
+    if constexpr (S::kRef)
+        return (sr_hash(seed ^ (uint32_t)i) + (uint32_t)((q + 1) >> 1) * 0x9E3779B9U) * 0x2C1B3C6DU;
     else return 0u;
+}
+
+// Encodes the 19 values d of a node and hands each to put(Q, value), Q an
+// std::integral_constant; ref(Q) is the reference density of the plane that
+// direction Q's value is stored for (16-bit formats).  The 16-bit formats round
+// the two values of each opposite pair (q odd, q + 1) with one conversion.
+template <class S, int Q, class Ref, class Put>
+__device__ __forceinline__ void encode_pair_(const typename S::M* d, uint32_t seed, int64_t i, Ref& ref, Put& put) {
+    using C0 = std::integral_constant<int, Q>;
+    using C1 = std::integral_constant<int, Q + 1>;
+    const uint32_t u = sr_key<S>(seed, i, Q);
+    if constexpr (S::kRef) {
+        const uint32_t h = S::template enc_sr2<Q>(d[Q], ref(C0{}), d[Q + 1], ref(C1{}), u);
+        put(C0{}, S::half_of(h, true));
+        put(C1{}, S::half_of(h, false));
+    } else {
+        put(C0{}, S::template enc_sr<Q>(d[Q], ref(C0{}), u));
+        put(C1{}, S::template enc_sr<Q + 1>(d[Q + 1], ref(C1{}), u));
+    }
+}
+template <class S, class Ref, class Put, int... P>
+__device__ __forceinline__ void encode_node_(const typename S::M* d, uint32_t seed, int64_t i, Ref& ref, Put& put,
+                                             std::integer_sequence<int, P...>) {
+    using C0 = std::integral_constant<int, 0>;
+    put(C0{}, S::template enc_sr<0>(d[0], ref(C0{}), sr_key<S>(seed, i, 0)));
+    (encode_pair_<S, 2 * P + 1>(d, seed, i, ref, put), ...);
+}
+template <class S, class Ref, class Put>
+__device__ __forceinline__ void encode_node(const typename S::M* d, uint32_t seed, int64_t i, Ref&& ref, Put&& put) {
+    encode_node_<S>(d, seed, i, ref, put, std::make_integer_sequence<int, 9>{});
 }
 
 // ------------------------------------------------------- boundary state ---
