@@ -58,8 +58,8 @@ struct Member {
 
 // LBM_BATCH16_PAIR_SCATTER: as LBM_AA16_PAIR_SCATTER, for the ensemble's
 // gather-scatter step.  Measured on the 64-pack FP16-dev ensemble, the
-// opposite order from the single lattice: the AA step pair takes 1.264 ms with
-// one conversion per pair and 1.316 ms with one per value.
+// opposite order from the single lattice: its AA step takes 1.234 ms with one
+// conversion per pair and 1.243 ms with one per value.
 #ifndef LBM_BATCH16_PAIR_SCATTER
 #define LBM_BATCH16_PAIR_SCATTER 1
 #endif
@@ -424,7 +424,7 @@ k_batch_aa(const Rows<typename S::T> F, int slot, const uint32_t* __restrict__ v
                     const int dq1 = __ldg(grid + ps + m.goff[Q]);      // and x - xi_Q that of Q
                     const uint32_t h = S::template enc_sr2<Q>(d[Q], dq >= 0 ? r_own + M(cz(Q)) * g : r_own, d[Q + 1],
                                                               dq1 >= 0 ? r_own - M(cz(Q)) * g : r_own,
-                                                              sr_key<S>(seed, i, Q));
+                                                              sr_key<S>(seed, i, Q), sr_key<S>(seed, i, Q + 1));
                     if (dq >= 0) F.row[Q][dq] = S::half_of(h, true);
                     else F.row[Q + 1][j] = S::half_of(h, true);
                     if (dq1 >= 0) F.row[Q + 1][dq1] = S::half_of(h, false);

@@ -59,8 +59,8 @@ constexpr int ZOUT = -2;
 // lower neighbour in units of the last place, so the rounding error has zero
 // mean.  Round-to-nearest would repeat the same error every step once the flow
 // is steady and bias the steady state.  The random bits come from a
-// counter-based hash of (step seed, node, direction pair), so a run is
-// reproducible.  Format conversions (encode, refresh) round to nearest.
+// counter-based hash of (step seed, node), so a run is reproducible.  Format
+// conversions (encode, refresh) round to nearest.
 //
 // The rounding is the conversion instruction cvt.rs.{f16x2,bf16x2}.f32 (PTX ISA
 // 8.7, sm_100a and later): it converts two FP32 values into one packed pair,
@@ -68,10 +68,28 @@ constexpr int ZOUT = -2;
 // magnitude and truncating.  Lane layout (measured on sm_103a with values
 // placed exactly below a rounding boundary, one rbits bit set at a time): the
 // value in the upper half takes rbits bits 16-28 (FP16: 13 discarded bits) or
-// 16-31 (BF16: 16), the value in the lower half bits 0-12 or 0-15.  So one
-// 32-bit key serves a pair of opposite directions (q odd, q + 1): q odd and the
-// rest direction 0 take the upper half, q even the lower half; enc_sr2 rounds
-// both values of a pair with one instruction.
+// 16-31 (BF16: 16), the value in the lower half bits 0-12 or 0-15; each half
+// depends on its own input only.  enc_sr2 rounds both values of an opposite
+// pair (q odd, q + 1) with one instruction.
+//
+// LBM_SR_MODE chooses the random numbers of a node's 19 values:
+//   2 (default): one random number per node for all 19 values;
+//   1: one per opposite pair, its two values on disjoint bit fields;
+//   0: one per direction (h + q * phi) * C, its top bits, as the conversion-
+//      free encode (add the bits, truncate) used before; gives identical states.
+// Each value is rounded without bias in every mode; what differs is how the
+// errors of a node's values are correlated.  With one number per node, an
+// opposite pair's errors are positively correlated (a large number rounds both
+// up), so they partly cancel in the momentum sum_q xi_q d_q.  Measured on a
+// 128^3 pack, 5000 steps from the FP64 steady state, L2 / max velocity error
+// against FP64: FP16-dev 3.7e-4 / 1.6e-3 (mode 2), 5.7e-4 / 7.2e-3 (mode 1),
+// 3.8e-4 / 2.9e-3 (mode 0); BF16-dev 3.0e-3 / 2.7e-2, 4.7e-3 / 5.9e-2,
+// 3.1e-3 / 2.6e-2; permeability within 6e-5 in all.  Mode 2 also needs no
+// per-value key arithmetic (FP16-dev AA step 0.1617 ms against 0.1660 and 0.1761).
+#ifndef LBM_SR_MODE
+#define LBM_SR_MODE 2
+#endif
+constexpr bool kSrSameField = LBM_SR_MODE == 2;
 constexpr float DEV_SCALE = 1024.0f;
 // Half of the packed stochastic conversion that direction q uses.
 __host__ __device__ constexpr bool sr_upper(int q) { return q == 0 || (q & 1); }
@@ -127,13 +145,17 @@ struct StoreF16 {
         return __ushort_as_half((unsigned short)(upper ? d >> 16 : d & 0xFFFFu));
     }
     template <int Q> __device__ static float scaled(M v, M r) { return fmaf(v, float(1024.0 / wq(Q)), -1024.0f * r); }
+    // rbits of the upper / lower half from a key (13-bit fields at bits 16 and 0)
+    __device__ static uint32_t bits_hi(uint32_t u) { return LBM_SR_MODE == 0 ? u >> 3 : u; }
+    __device__ static uint32_t bits_lo(uint32_t u) { return LBM_SR_MODE == 0 ? u >> 19 : u; }
     template <int Q> __device__ static T enc_sr(M v, M r, uint32_t u) {
-        constexpr bool up = sr_upper(Q);
-        return half_of(up ? cvt_rs(scaled<Q>(v, r), 0.0f, u) : cvt_rs(0.0f, scaled<Q>(v, r), u), up);
+        constexpr bool up = sr_upper(Q) && !kSrSameField;
+        return half_of(up ? cvt_rs(scaled<Q>(v, r), 0.0f, bits_hi(u)) : cvt_rs(0.0f, scaled<Q>(v, r), bits_lo(u)), up);
     }
-    template <int Q> __device__ static uint32_t enc_sr2(M v, M r, M v1, M r1, uint32_t u) {
+    template <int Q> __device__ static uint32_t enc_sr2(M v, M r, M v1, M r1, uint32_t u, uint32_t u1) {
         static_assert(Q & 1, "a pair starts at an odd direction");
-        return cvt_rs(scaled<Q>(v, r), scaled<Q + 1>(v1, r1), u);
+        return cvt_rs(scaled<Q>(v, r), scaled<Q + 1>(v1, r1),
+                      LBM_SR_MODE == 0 ? ((bits_hi(u) & 0xFFFF0000u) | bits_lo(u1)) : u);
     }
 };
 struct StoreBF16 {
@@ -155,27 +177,39 @@ struct StoreBF16 {
         return __ushort_as_bfloat16((unsigned short)(upper ? d >> 16 : d & 0xFFFFu));
     }
     template <int Q> __device__ static float scaled(M v, M r) { return fmaf(v, float(1024.0 / wq(Q)), -1024.0f * r); }
+    // rbits of the upper / lower half from a key (16-bit fields at bits 16 and 0)
+    __device__ static uint32_t bits_hi(uint32_t u) { return u; }
+    __device__ static uint32_t bits_lo(uint32_t u) { return LBM_SR_MODE == 0 ? u >> 16 : u; }
     template <int Q> __device__ static T enc_sr(M v, M r, uint32_t u) {
-        constexpr bool up = sr_upper(Q);
-        return half_of(up ? cvt_rs(scaled<Q>(v, r), 0.0f, u) : cvt_rs(0.0f, scaled<Q>(v, r), u), up);
+        constexpr bool up = sr_upper(Q) && !kSrSameField;
+        return half_of(up ? cvt_rs(scaled<Q>(v, r), 0.0f, bits_hi(u)) : cvt_rs(0.0f, scaled<Q>(v, r), bits_lo(u)), up);
     }
-    template <int Q> __device__ static uint32_t enc_sr2(M v, M r, M v1, M r1, uint32_t u) {
+    template <int Q> __device__ static uint32_t enc_sr2(M v, M r, M v1, M r1, uint32_t u, uint32_t u1) {
         static_assert(Q & 1, "a pair starts at an odd direction");
-        return cvt_rs(scaled<Q>(v, r), scaled<Q + 1>(v1, r1), u);
+        return cvt_rs(scaled<Q>(v, r), scaled<Q + 1>(v1, r1),
+                      LBM_SR_MODE == 0 ? ((u & 0xFFFF0000u) | bits_lo(u1)) : u);
     }
 };
 
 // Random bits of the stochastic rounding of value (node i, direction q) in the
 // step with seed `seed` (no work for the formats that store exactly): one hash
-// per node (the same call for every q, computed once), then a Weyl step per
-// direction pair (q + 1) / 2 mixed by one multiply.  The pair's two values take
-// disjoint bit fields of the product (see the codecs), so they are rounded
-// independently.
+// per node (the same call for every q, computed once).  Mode 2 places its upper
+// 16 bits in both halves of the rbits word, so either half of a conversion
+// draws the same number; modes 0 and 1 add a Weyl step per direction or pair
+// and mix it by one multiply.
 template <class S>
 __device__ __forceinline__ uint32_t sr_key(uint32_t seed, int64_t i, int q) {
-    if constexpr (S::kRef)
-        return (sr_hash(seed ^ (uint32_t)i) + (uint32_t)((q + 1) >> 1) * 0x9E3779B9U) * 0x2C1B3C6DU;
-    else return 0u;
+    if constexpr (S::kRef) {
+        const uint32_t h = sr_hash(seed ^ (uint32_t)i);
+        if constexpr (LBM_SR_MODE == 2) {
+            (void)q;
+            return __byte_perm(h, 0u, 0x3232u);
+        } else {
+            return (h + (uint32_t)(LBM_SR_MODE == 1 ? (q + 1) >> 1 : q) * 0x9E3779B9U) * 0x2C1B3C6DU;
+        }
+    } else {
+        return 0u;
+    }
 }
 
 // Encodes the 19 values d of a node and hands each to put(Q, value), Q an
@@ -188,7 +222,7 @@ __device__ __forceinline__ void encode_pair_(const typename S::M* d, uint32_t se
     using C1 = std::integral_constant<int, Q + 1>;
     const uint32_t u = sr_key<S>(seed, i, Q);
     if constexpr (S::kRef) {
-        const uint32_t h = S::template enc_sr2<Q>(d[Q], ref(C0{}), d[Q + 1], ref(C1{}), u);
+        const uint32_t h = S::template enc_sr2<Q>(d[Q], ref(C0{}), d[Q + 1], ref(C1{}), u, sr_key<S>(seed, i, Q + 1));
         put(C0{}, S::half_of(h, true));
         put(C1{}, S::half_of(h, false));
     } else {

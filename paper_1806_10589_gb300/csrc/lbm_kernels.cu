@@ -481,8 +481,8 @@ struct AAPtrs {
 #endif
 // LBM_AA16_PAIR_SCATTER: 1 = the 16-bit gather-scatter step rounds each
 // opposite pair with one conversion before its two stores, 0 = one conversion
-// per value next to its store.  Measured on the 256^3 pack: 0 is 6.5 % (FP16)
-// and 4.4 % (BF16) faster in that launch (the node-local launch rounds pairs).
+// per value next to its store.  Measured on the 256^3 pack: 0 is 2.9 % (FP16)
+// and 2.8 % (BF16) faster in that launch (the node-local launch rounds pairs).
 #ifndef LBM_AA16_PAIR_SCATTER
 #define LBM_AA16_PAIR_SCATTER 0
 #endif
@@ -607,7 +607,7 @@ k_step_aa(const AAPtrs<typename S::T> F, int slot, DevLattice L, typename S::M s
                     const int dq1 = dest(qc_t<Q + 1>{});
                     const uint32_t h = S::template enc_sr2<Q>(d[Q], dq >= 0 ? r_own + M(cz(Q)) * g : r_own, d[Q + 1],
                                                               dq1 >= 0 ? r_own - M(cz(Q)) * g : r_own,
-                                                              sr_key<S>(seed, i, Q));
+                                                              sr_key<S>(seed, i, Q), sr_key<S>(seed, i, Q + 1));
                     *(dq >= 0 ? F.row[Q] + dq : F.row[Q + 1] + j) = S::half_of(h, true);
                     *(dq1 >= 0 ? F.row[Q + 1] + dq1 : F.row[Q] + j) = S::half_of(h, false);
                 });
