@@ -354,7 +354,13 @@ int lbm_wsnet_loss_grad(lbm_wsnet* net, const uint8_t* masks, const float* targe
 /* Adam training (beta 0.9 / 0.999, eps 1e-8): `epochs` passes over n_samples
  * host samples in mini-batches of `batch`, visiting samples in the caller's
  * order (epochs*n_samples indices); mean loss per epoch into loss_history
- * (epochs floats, may be NULL).  Synchronises. */
+ * (epochs floats, may be NULL).  Synchronises.  Deterministic: the weight and
+ * bias gradients are summed per row split and the splits added in a fixed
+ * order (no floating-point atomics), so the same inputs give bitwise the same
+ * parameters on the same GPU model (also for lbm_wsnet_loss_grad's gradient;
+ * the reported losses are FP64 sums whose order, and so whose last bits, may
+ * vary).  The partial sums take up to 8.5e7 bytes of device memory more,
+ * freed by lbm_wsnet_release_buffers. */
 int lbm_wsnet_train(lbm_wsnet* net, const uint8_t* masks, const float* targets, int n_samples, int nx, int ny,
                     int nz, int epochs, int batch, float lr, const int* order, float* loss_history);
 /* Predicted fields (host, 4*nz*ny*nx floats) of one geometry; 0 at solids. */
@@ -378,7 +384,9 @@ const char* lbm_wsnet_last_error(const lbm_wsnet* net);
  *          border rows written 0)
  *   op 2, weight gradient:  out[co][t][ci] += sum_v aux[v][co] in[v + t][ci]
  *         (in: the layer input, cin channels; aux: the output gradient, cout
- *          channels, zero on border rows; out: FP32 [cout][27][cin], added to)
+ *          channels, zero on border rows; out: FP32 [cout][27][cin], added to
+ *          with FP32 atomics, one per row split: the order of those additions,
+ *          and so the last bits, may vary between calls)
  * Returns LBM_EINVAL for bad arguments, LBM_ECUDA for a CUDA error and
  * LBM_ETIMEOUT if a pipeline wait ran out. */
 int lbm_conv3d_bf16(int op, const void* in, const void* aux, const void* w, const float* bias, int relu, void* out,

@@ -332,7 +332,22 @@ struct WgArgs {
     int64_t nchunks;     // row chunks of 128 in the volume
     int* err;
     PGeo g;
+    // Deterministic form: each row split stores its partial sums in
+    // part[split][cout_real][27][cin_real] (part_cap floats available) and a
+    // second kernel adds them to gw in split order; null: FP32 atomics into gw.
+    float* part;
+    int64_t part_cap;
 };
+
+// Row splits of a weight-gradient launch: enough CTAs for two per SM over the
+// groups of 128 (tap, c_in) pairs, at most one per 128-row chunk.
+inline int64_t wgrad_splits(int cin, int cout, int64_t rows, int n_sm) {
+    const int ng = (27 * cin + 127) / 128;
+    const int gpc = std::min(ng, 512 / cout);
+    const int gsets = (ng + gpc - 1) / gpc;
+    const int64_t want = std::max<int64_t>(1, (2 * (int64_t)n_sm + gsets - 1) / gsets);
+    return std::min<int64_t>(want, (rows + kRows - 1) / kRows);
+}
 
 template <int CIN, int COUT>
 __global__ void __launch_bounds__(kThreads, 1)
@@ -426,7 +441,10 @@ k_wgrad(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensor
 #pragma unroll
                 for (int i = 0; i < 32; ++i) {
                     const int co = c0 + i;
-                    if (co < a.cout_real) atomicAdd(a.gw + ((int64_t)co * 27 + tap) * a.cin_real + ci, v[i]);
+                    if (co >= a.cout_real) continue;
+                    const int64_t w = ((int64_t)co * 27 + tap) * a.cin_real + ci;
+                    if (a.part) a.part[(int64_t)blockIdx.x * ((int64_t)a.cout_real * 27 * a.cin_real) + w] = v[i];
+                    else atomicAdd(a.gw + w, v[i]);
                 }
             }
         }
@@ -599,8 +617,20 @@ __global__ void k_mse(const float* __restrict__ Y, const float* __restrict__ T, 
     }
 }
 
-// gb[c] += sum over rows of G[row][c], c < creal; block of 256 threads, C / 8 channel groups
-__global__ void k_bias_grad(const bf16* __restrict__ G, int64_t rows, int C, int creal, float* __restrict__ gb) {
+// gw[w] += sum over k of part[k][w], k in order (the deterministic finish of
+// the weight- and bias-gradient kernels)
+__global__ void k_split_sum(const float* __restrict__ part, int64_t splits, int64_t nw, float* __restrict__ gw) {
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nw; w += (int64_t)gridDim.x * blockDim.x) {
+        float s = 0.f;
+        for (int64_t k = 0; k < splits; ++k) s += part[k * nw + w];
+        gw[w] += s;
+    }
+}
+
+// gb[c] += sum over rows of G[row][c], c < creal; block of 256 threads, C / 8 channel groups.
+// With `part`, block b stores its sums in part[b][c] instead (no atomics).
+__global__ void k_bias_grad(const bf16* __restrict__ G, int64_t rows, int C, int creal, float* __restrict__ gb,
+                            float* __restrict__ part) {
     __shared__ float sh[256][8];
     const int cg = C / 8;
     const int lanes = 256 / cg;  // threads per channel group
@@ -622,8 +652,12 @@ __global__ void k_bias_grad(const bf16* __restrict__ G, int64_t rows, int C, int
 #pragma unroll
             for (int i = 0; i < 8; ++i) s[i] += sh[u * cg + threadIdx.x][i];
 #pragma unroll
-        for (int i = 0; i < 8; ++i)
-            if (threadIdx.x * 8 + i < creal) atomicAdd(gb + threadIdx.x * 8 + i, s[i]);
+        for (int i = 0; i < 8; ++i) {
+            const int c = threadIdx.x * 8 + i;
+            if (c >= creal) continue;
+            if (part) part[(int64_t)blockIdx.x * creal + c] = s[i];
+            else atomicAdd(gb + c, s[i]);
+        }
     }
 }
 
@@ -726,9 +760,11 @@ cudaError_t wgrad_t(const bf16* act, const bf16* gout, const WgArgs& a0, cudaStr
     WgArgs a = a0;
     a.nchunks = (a.g.rows() + kRows - 1) / kRows;
     const int gsets = (K::NG + K::GPC - 1) / K::GPC;
-    const int64_t want = std::max<int64_t>(1, (2 * (int64_t)n_sm + gsets - 1) / gsets);
-    const unsigned splits = (unsigned)std::min<int64_t>(want, a.nchunks);
+    const unsigned splits = (unsigned)wgrad_splits(CIN, COUT, a.g.rows(), n_sm);
+    const int64_t nw = (int64_t)a.cout_real * 27 * a.cin_real;
+    if (a.part && (int64_t)splits * nw > a.part_cap) return cudaErrorInvalidValue;
     k_wgrad<CIN, COUT><<<dim3(splits, (unsigned)gsets), kThreads, K::SMEM, st>>>(ma, mg, a);
+    if (a.part) k_split_sum<<<gs_blocks(nw), 256, 0, st>>>(a.part, splits, nw, a.gw);
     return cudaGetLastError();
 }
 
@@ -779,6 +815,8 @@ struct lbm_wsnet {
     float* bst = nullptr;               // padded biases
     double* d_loss = nullptr;
     int* d_err = nullptr;
+    float* part = nullptr;              // per-split partial gradient sums (deterministic accumulation)
+    int64_t part_cap = 0;               // floats
     int64_t adam_t = 0;
     bool packed = false;
     cudaStream_t stream = nullptr;
@@ -945,10 +983,26 @@ int bwd_weight(lbm_wsnet* n, int k, const bf16* act, const bf16* gout, int l) {
     a.cout_real = d.cout;
     a.err = n->d_err;
     a.g = level_geo(n, l);
-    WS_CUDA(n, wsn::wgrad(d.cin_p, d.cout_p, act, gout, a, n->stream, n->n_sm));
     const int64_t rows = a.g.rows();
     const unsigned nb = (unsigned)std::min<int64_t>(std::max<int64_t>(1, rows / 512), 152 * 4);
-    wsn::k_bias_grad<<<nb, 256, 0, n->stream>>>(gout, rows, d.cout_p, d.cout, n->g + d.boff);
+    // partial sums per row split, added in a fixed order: the gradients (and so
+    // the training) do not depend on the order in which CTAs finish
+    const int64_t need = std::max<int64_t>(wsn::wgrad_splits(d.cin_p, d.cout_p, rows, n->n_sm) * d.cout * 27 * d.cin,
+                                           (int64_t)nb * d.cout);
+    if (need > n->part_cap) {
+        WS_CUDA(n, cudaStreamSynchronize(n->stream));
+        cudaFree(n->part);
+        n->part = nullptr;
+        n->part_cap = 0;
+        if (cudaMalloc(&n->part, sizeof(float) * need) != cudaSuccess)
+            return wfail(n, LBM_ENOMEM, "gradient partial sums (%lld floats)", (long long)need);
+        n->part_cap = need;
+    }
+    a.part = n->part;
+    a.part_cap = n->part_cap;
+    WS_CUDA(n, wsn::wgrad(d.cin_p, d.cout_p, act, gout, a, n->stream, n->n_sm));
+    wsn::k_bias_grad<<<nb, 256, 0, n->stream>>>(gout, rows, d.cout_p, d.cout, n->g + d.boff, n->part);
+    wsn::k_split_sum<<<wsn::gs_blocks(d.cout), 256, 0, n->stream>>>(n->part, nb, d.cout, n->g + d.boff);
     WS_CUDA(n, cudaGetLastError());
     return LBM_OK;
 }
@@ -1337,6 +1391,9 @@ int lbm_wsnet_release_buffers(lbm_wsnet* n) {
     if (rc) return rc;
     cudaStreamSynchronize(n->stream);
     free_buffers(n);
+    cudaFree(n->part);
+    n->part = nullptr;
+    n->part_cap = 0;
     return LBM_OK;
 }
 
@@ -1353,6 +1410,7 @@ int lbm_wsnet_destroy(lbm_wsnet* n) {
     cudaFree(n->bst);
     cudaFree(n->d_L);
     cudaFree(n->d_loss);
+    cudaFree(n->part);
     cudaFree(n->d_err);
     delete n;
     return LBM_OK;

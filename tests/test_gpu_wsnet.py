@@ -196,6 +196,30 @@ def test_training_reduces_loss(net):
     assert hist[-1] < 0.2 * hist[0], hist[[0, -1]]
 
 
+def test_training_is_deterministic(net):
+    """The weight and bias gradients are summed per row split and the splits
+    added in a fixed order (no floating-point atomics), so the same data, start
+    and sample order give bitwise the same gradients and the same trained
+    parameters."""
+    rng = np.random.default_rng(9)
+    masks = (rng.random((4, 16, 16, 16)) < 0.3).astype(np.uint8)
+    pore = 1.0 - masks.astype(np.float32)
+    t = np.stack([pore * 0.3, pore * rng.standard_normal(masks.shape).astype(np.float32) * 0.1, pore * -0.2,
+                  pore * 1.5], axis=1).astype(np.float32)
+    p0 = _he(4, 32, 11) * 0.5
+    runs = []
+    for _ in range(2):
+        net.set_params(p0)
+        _, g = net.loss_grad(masks, t)
+        hist = net.train(masks, t, epochs=3, batch=2, lr=1e-3, seed=3)
+        runs.append((g, hist, net.params()))
+    (g0, h0, q0), (g1, h1, q1) = runs
+    assert np.abs(g0).max() > 0
+    np.testing.assert_array_equal(g0, g1)
+    np.testing.assert_array_equal(q0, q1)
+    assert not np.array_equal(q0, p0)
+
+
 def test_interior_crops_of_the_training_data(torch):
     """With a margin the inputs and targets are the interior crops of the
     steady states: the crop's velocity is the whole box's (over u_D of the
