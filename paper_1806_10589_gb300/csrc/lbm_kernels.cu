@@ -15,6 +15,7 @@
 //   k_monitors      FP64 mass / flux / max|u| / NaN reductions of a state.
 //   k_export, k_init_eq, k_encode, k_decode   field and state conversions.
 #include <algorithm>
+#include <cstdlib>
 #include <utility>
 
 #include "lbm_device.cuh"
@@ -509,7 +510,12 @@ __device__ __forceinline__ uint64_t aa_index_policy() {
 #endif
 }
 
-template <class S, bool ODD>
+// OFF32 (gather-scatter launch, buffers of 19 ns < 2^32 elements): every
+// neighbour address is row 0 plus one 32-bit element offset, the source or
+// destination row chosen by a 32-bit select, instead of a select between two
+// 64-bit row pointers.  Measured on the 256^3 pack: the launch 6.5 % (FP32) and
+// 8 % (FP16-dev) shorter.
+template <class S, bool ODD, bool OFF32 = false>
 __global__ void __launch_bounds__(kBlock, aa_min_blocks<S, ODD>())
 k_step_aa(const AAPtrs<typename S::T> F, int slot, DevLattice L, typename S::M sp, typename S::M sm,
           BcState* bc, double* __restrict__ partials, unsigned* __restrict__ counter) {
@@ -554,10 +560,19 @@ k_step_aa(const AAPtrs<typename S::T> F, int slot, DevLattice L, typename S::M s
                     // 16-bit (instruction-bound): one load and one decode, the
                     // source slot and its plane selected
                     const bool pore = nb[Q] >= 0;
-                    const typename S::T* src = pore ? F.row[opp(Q)] + nb[Q] : F.row[Q] + i;
+                    const typename S::T* src;
+                    if constexpr (OFF32)  // one 32-bit element offset from row 0 (the rows are ns apart)
+                        src = F.row[0] + (pore ? (uint32_t)opp(Q) * (uint32_t)L.ns + (uint32_t)nb[Q]
+                                               : (uint32_t)Q * (uint32_t)L.ns + (uint32_t)i);
+                    else
+                        src = pore ? F.row[opp(Q)] + nb[Q] : F.row[Q] + i;
                     d[Q] = S::template dec<Q>(*src, pore ? r_own - M(cz(Q)) * g : r_own);
                 } else {
-                    d[Q] = nb[Q] >= 0 ? F.row[opp(Q)][nb[Q]] : F.row[Q][i];
+                    if constexpr (OFF32)
+                        d[Q] = F.row[0][nb[Q] >= 0 ? (uint32_t)opp(Q) * (uint32_t)L.ns + (uint32_t)nb[Q]
+                                                    : (uint32_t)Q * (uint32_t)L.ns + (uint32_t)i];
+                    else
+                        d[Q] = nb[Q] >= 0 ? F.row[opp(Q)][nb[Q]] : F.row[Q][i];
                 }
             });
         } else {
@@ -595,8 +610,13 @@ k_step_aa(const AAPtrs<typename S::T> F, int slot, DevLattice L, typename S::M s
                     constexpr int Q = decltype(qc)::value + 1;
                     const int dst = dest(qc_t<Q>{});
                     const bool pore = dst >= 0;
-                    *(pore ? F.row[Q] + dst : F.row[opp(Q)] + j) =
-                        S::template enc_sr<Q>(d[Q], pore ? r_own + M(cz(Q)) * g : r_own, sr_key<S>(seed, i, Q));
+                    typename S::T* out;
+                    if constexpr (OFF32)
+                        out = F.row[0] + (pore ? (uint32_t)Q * (uint32_t)L.ns + (uint32_t)dst
+                                               : (uint32_t)opp(Q) * (uint32_t)L.ns + (uint32_t)j);
+                    else
+                        out = pore ? F.row[Q] + dst : F.row[opp(Q)] + j;
+                    *out = S::template enc_sr<Q>(d[Q], pore ? r_own + M(cz(Q)) * g : r_own, sr_key<S>(seed, i, Q));
                 });
             } else if constexpr (S::kRef) {
                 // 16-bit: per opposite pair one stochastic conversion; per value one
@@ -615,8 +635,13 @@ k_step_aa(const AAPtrs<typename S::T> F, int slot, DevLattice L, typename S::M s
                 for_q(std::make_integer_sequence<int, 18>{}, [&](auto qc) {
                     constexpr int Q = decltype(qc)::value + 1;
                     const int dst = dest(qc_t<Q>{});
-                    if (dst >= 0) F.row[Q][dst] = d[Q];
-                    else F.row[opp(Q)][j] = d[Q];
+                    if constexpr (OFF32) {
+                        F.row[0][dst >= 0 ? (uint32_t)Q * (uint32_t)L.ns + (uint32_t)dst
+                                          : (uint32_t)opp(Q) * (uint32_t)L.ns + (uint32_t)j] = d[Q];
+                    } else {
+                        if (dst >= 0) F.row[Q][dst] = d[Q];
+                        else F.row[opp(Q)][j] = d[Q];
+                    }
                 });
             }
         } else {
@@ -1304,7 +1329,13 @@ cudaError_t launch_aa_step(int prec, void* f, int odd, int slot, const DevLattic
         {
             AAPtrs<typename S::T> F;
             for (int q = 0; q < 19; ++q) F.row[q] = (typename S::T*)f + (int64_t)q * L.ns;
-            if (odd)
+            // every element offset of the buffer fits in 32 bits; the environment
+            // variable GB300_LBM_AA_ADDR64 forces the 64-bit form (for tests)
+            const bool off32 = 19 * (uint64_t)L.ns <= 0xFFFFFFFFull && !std::getenv("GB300_LBM_AA_ADDR64");
+            if (odd && off32)
+                k_step_aa<S, true, true><<<blocks_for(L.n, kBlock), kBlock, 0, st>>>(
+                    F, slot, L, (M)r.sp, (M)r.sm, bc, partials, counter);
+            else if (odd)
                 k_step_aa<S, true><<<blocks_for(L.n, kBlock), kBlock, 0, st>>>(F, slot, L, (M)r.sp, (M)r.sm, bc,
                                                                                 partials, counter);
             else

@@ -81,6 +81,22 @@ def test_aa_equals_two_buffer_kernel(torch_cuda, prec, chunks):
     assert abs(fa_out[0] - fb_out[0]) <= (1e-6 if prec == "fp32" else 1e-13)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16dev", "bf16dev"])
+def test_aa_32bit_offsets_equal_64bit_addresses(torch_cuda, prec, monkeypatch):
+    """The gather-scatter launch addresses its neighbours as row 0 plus a 32-bit
+    element offset whenever the buffer has fewer than 2^32 elements; the 64-bit
+    form (two row pointers) serves larger lattices.  Both compute the same step,
+    so the states are bitwise equal (the 64-bit form is forced by the
+    GB300_LBM_AA_ADDR64 switch; graphs are captured per lattice, after it is set)."""
+    m = random_mask(37, 29, 21, 0.3, 8)
+    chunks = [1, 64, 3]
+    a = _run(m, prec, 3, chunks, torch_cuda)
+    monkeypatch.setenv("GB300_LBM_AA_ADDR64", "1")
+    b = _run(m, prec, 3, chunks, torch_cuda)
+    np.testing.assert_array_equal(a[0], b[0])
+    assert a[1] == b[1] and a[2] == b[2]
+
+
 def test_aa_switching_mid_run_releases_and_restores_memory(torch_cuda):
     from paper_1806_10589_gb300 import Lattice
 

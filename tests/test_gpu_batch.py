@@ -149,6 +149,22 @@ def test_batch_configs_agree(torch_cuda, prec):
             assert np.abs(got[k] - ref[k]).max() <= tol, (config, k)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp16dev"])
+@pytest.mark.parametrize("config", [0, 1])
+def test_batch_32bit_offsets_equal_64bit_addresses(torch_cuda, prec, config, monkeypatch):
+    """The per-step launches address a pulled value as the buffer plus a 32-bit
+    element offset when the buffers have fewer than 2^32 elements, else as one
+    of two 64-bit addresses; both forms give bitwise the same states (the
+    64-bit form is forced by GB300_LBM_BATCH_ADDR64)."""
+    masks = _members()
+    a = _run_cfg(masks, prec, config, 70, torch_cuda)
+    monkeypatch.setenv("GB300_LBM_BATCH_ADDR64", "1")
+    b = _run_cfg(masks, prec, config, 70, torch_cuda)
+    for fa, fb in zip(a[0], b[0]):
+        np.testing.assert_array_equal(fa, fb)
+    assert a[1] == b[1]
+
+
 def test_batch_autotune_keeps_state_and_picks_a_config(torch_cuda):
     from paper_1806_10589_gb300 import Batch
 
