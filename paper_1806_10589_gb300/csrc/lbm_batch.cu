@@ -373,7 +373,7 @@ struct Rows {
     T* row[19];
 };
 
-template <class S, bool ODD, int MINB>
+template <class S, bool ODD, int MINB, bool OFF32 = false>
 __global__ void __launch_bounds__(kTile, batch_min_blocks<S, MINB>())
 k_batch_aa(const Rows<typename S::T> F, int slot, const uint32_t* __restrict__ vox,
            const int* __restrict__ grid, const int* __restrict__ tile_member, Member* members, typename S::M sp,
@@ -395,11 +395,25 @@ k_batch_aa(const Rows<typename S::T> F, int slot, const uint32_t* __restrict__ v
         M d[19];
         if constexpr (ODD) {
             d[0] = S::template dec<0>(F.row[0][i], r_own);
+            const uint32_t ns32 = (uint32_t)(F.row[1] - F.row[0]);  // rows are ns apart, as launched
             for_q(std::make_integer_sequence<int, 18>{}, [&](auto qc) {
                 constexpr int Q = decltype(qc)::value + 1;
                 const int id = __ldg(grid + p + m.goff[Q]);
-                d[Q] = id >= 0 ? S::template dec<Q>(F.row[opp(Q)][id], r_own - M(cz(Q)) * g)
-                               : S::template dec<Q>(F.row[Q][i], r_own);
+                if constexpr (OFF32) {
+                    const bool pore = id >= 0;
+                    d[Q] = S::template dec<Q>(F.row[0][pore ? (uint32_t)opp(Q) * ns32 + (uint32_t)id
+                                                            : (uint32_t)Q * ns32 + (uint32_t)i],
+                                              pore ? r_own - M(cz(Q)) * g : r_own);
+                } else {
+                    d[Q] = id >= 0 ? S::template dec<Q>(F.row[opp(Q)][id], r_own - M(cz(Q)) * g)
+                                   : S::template dec<Q>(F.row[Q][i], r_own);
+                }
+            });
+        } else if constexpr (OFF32) {
+            const uint32_t ns32 = (uint32_t)(F.row[1] - F.row[0]);
+            for_q(AllQ{}, [&](auto qc) {
+                constexpr int Q = decltype(qc)::value;
+                d[Q] = S::template dec<Q>(F.row[0][(uint32_t)Q * ns32 + (uint32_t)i], r_own);
             });
         } else {
             for_q(AllQ{}, [&](auto qc) {
@@ -420,7 +434,17 @@ k_batch_aa(const Rows<typename S::T> F, int slot, const uint32_t* __restrict__ v
         if constexpr (ODD) {
             const int64_t ps = __ldg(vox + j);
             F.row[0][j] = S::template enc_sr<0>(d[0], r_own, sr_key<S>(seed, i, 0));
-            if constexpr (S::kRef && !LBM_BATCH16_PAIR_SCATTER) {
+            if constexpr (OFF32) {
+                // one store per value at row 0 plus a 32-bit offset, destination row and plane selected
+                const uint32_t ns32 = (uint32_t)(F.row[1] - F.row[0]);
+                for_q(std::make_integer_sequence<int, 18>{}, [&](auto qc) {
+                    constexpr int Q = decltype(qc)::value + 1;
+                    const int dst = __ldg(grid + ps + m.goff[opp(Q)]);  // x + xi_Q is the pull source of opp(Q)
+                    const bool pore = dst >= 0;
+                    F.row[0][pore ? (uint32_t)Q * ns32 + (uint32_t)dst : (uint32_t)opp(Q) * ns32 + (uint32_t)j] =
+                        S::template enc_sr<Q>(d[Q], pore ? r_own + M(cz(Q)) * g : r_own, sr_key<S>(seed, i, Q));
+                });
+            } else if constexpr (S::kRef && !LBM_BATCH16_PAIR_SCATTER) {
                 for_q(std::make_integer_sequence<int, 18>{}, [&](auto qc) {
                     constexpr int Q = decltype(qc)::value + 1;
                     const int dst = __ldg(grid + ps + m.goff[opp(Q)]);  // x + xi_Q is the pull source of opp(Q)
@@ -450,6 +474,12 @@ k_batch_aa(const Rows<typename S::T> F, int slot, const uint32_t* __restrict__ v
                     else F.row[opp(Q)][j] = d[Q];
                 });
             }
+        } else if constexpr (OFF32) {
+            const uint32_t ns32 = (uint32_t)(F.row[1] - F.row[0]);
+            encode_node<S>(d, seed, i, [&](auto) { return r_own; }, [&](auto qc, typename S::T v) {
+                constexpr int Q = decltype(qc)::value;
+                F.row[0][(uint32_t)opp(Q) * ns32 + (uint32_t)j] = v;
+            });
         } else {
             encode_node<S>(d, seed, i, [&](auto) { return r_own; }, [&](auto qc, typename S::T v) {
                 constexpr int Q = decltype(qc)::value;
@@ -886,9 +916,15 @@ int bstep_aa(lbm_batch* b, cudaStream_t st, bool odd) {
             constexpr int MINB = decltype(minbc)::value;
             lbm::Rows<T> F;
             for (int q = 0; q < 19; ++q) F.row[q] = (T*)b->f[0] + (int64_t)q * b->ns;
-            lbm::k_batch_aa<S, ODD, MINB><<<(unsigned)b->ntiles, lbm::kTile, 0, st>>>(
-                F, b->cur, b->d_vox, b->d_grid, b->d_tile_member, b->d_members, (M)b->sp, (M)b->sm,
-                b->d_partials, b->d_counters);
+            // OFF32 when every element offset fits in 32 bits
+            if (19 * (uint64_t)b->ns <= 0xFFFFFFFFull && !std::getenv("GB300_LBM_BATCH_ADDR64"))
+                lbm::k_batch_aa<S, ODD, MINB, true><<<(unsigned)b->ntiles, lbm::kTile, 0, st>>>(
+                    F, b->cur, b->d_vox, b->d_grid, b->d_tile_member, b->d_members, (M)b->sp, (M)b->sm,
+                    b->d_partials, b->d_counters);
+            else
+                lbm::k_batch_aa<S, ODD, MINB><<<(unsigned)b->ntiles, lbm::kTile, 0, st>>>(
+                    F, b->cur, b->d_vox, b->d_grid, b->d_tile_member, b->d_members, (M)b->sp, (M)b->sm,
+                    b->d_partials, b->d_counters);
         };
         const bool capped = cfg_capped(b->config);
         if (odd && capped) go(std::true_type{}, std::integral_constant<int, 5>{});
