@@ -22,6 +22,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -188,7 +189,10 @@ constexpr int color_min_blocks() {
     return sizeof(T) == 8 ? 1 : LBM_COLOR_MIN_BLOCKS;
 }
 
-template <class T>
+// OFF32 (buffers of 19 ns < 2^32 elements): a gathered momentum value and a
+// pushed D3Q7 value are addressed as row 0 plus one 32-bit element offset, the
+// row chosen by a 32-bit select (as in the single-fluid gather-scatter step).
+template <class T, bool OFF32 = false>
 __global__ void __launch_bounds__(kCB, color_min_blocks<T>())
 k_color_step(const ColorRows<T> R, const T* __restrict__ phi, DevLattice L, const ColorParams* __restrict__ prm,
              T sp, T sm, T alpha, T beta, T phi_s) {
@@ -216,7 +220,11 @@ k_color_step(const ColorRows<T> R, const T* __restrict__ phi, DevLattice L, cons
     for_q(std::make_integer_sequence<int, 18>{}, [&](auto qc) {
         constexpr int Q = decltype(qc)::value + 1;
         const int id = ld_hint(L.grid + (uint32_t)(p + (uint32_t)grid_off<Q>(L.sy, L.sz)), pol);
-        d[Q] = id >= 0 ? R.fin[Q][id] : R.fin[opp(Q)][i];
+        if constexpr (OFF32)
+            d[Q] = R.fin[0][id >= 0 ? (uint32_t)Q * (uint32_t)L.ns + (uint32_t)id
+                                    : (uint32_t)opp(Q) * (uint32_t)L.ns + (uint32_t)i];
+        else
+            d[Q] = id >= 0 ? R.fin[Q][id] : R.fin[opp(Q)][i];
         // colour-gradient neighbour x + xi_opp(Q) is the pull source of Q
         const T ph = id >= 0 ? phi[id] : (id == SOLID ? phi_s : phi_own);  // box faces: own phi
         constexpr int Rq = opp(Q);  // this neighbour sits at x + xi_Rq
@@ -272,7 +280,14 @@ k_color_step(const ColorRows<T> R, const T* __restrict__ phi, DevLattice L, cons
         } else {
             // push destination x + xi_Q is the pull source of opp(Q)
             const int id = ld_hint(L.grid + (uint32_t)(ps + (uint32_t)grid_off<opp(Q)>(L.sy, L.sz)), pol);
-            if (id >= 0) {
+            if constexpr (OFF32) {
+                if (id != ZOUT) {  // a pore, or bounce-back from a solid voxel or lateral box face
+                    const uint32_t off = id >= 0 ? (uint32_t)Q * (uint32_t)L.ns + (uint32_t)id
+                                                 : (uint32_t)opp(Q) * (uint32_t)L.ns + (uint32_t)j;
+                    R.aout[0][off] = va;
+                    R.bout[0][off] = vb;
+                }
+            } else if (id >= 0) {
                 R.aout[Q][id] = va;
                 R.bout[Q][id] = vb;
             } else if (id != ZOUT) {  // solid voxel or lateral box face: bounce back
@@ -469,8 +484,12 @@ int cstep_once(lbm_color* c) {
             R.bin[q] = (const T*)c->B[k] + (int64_t)q * c->L.ns;
             R.bout[q] = (T*)c->B[k ^ 1] + (int64_t)q * c->L.ns;
         }
-        lbm::k_color_step<T><<<nb, lbm::kCB, 0, c->stream>>>(R, (const T*)c->phi, c->L, c->d_prm, (T)c->sp,
-                                                             (T)c->sm, (T)c->alpha, (T)c->beta, (T)c->phi_s);
+        if (19 * (uint64_t)c->L.ns <= 0xFFFFFFFFull && !std::getenv("GB300_LBM_COLOR_ADDR64"))
+            lbm::k_color_step<T, true><<<nb, lbm::kCB, 0, c->stream>>>(
+                R, (const T*)c->phi, c->L, c->d_prm, (T)c->sp, (T)c->sm, (T)c->alpha, (T)c->beta, (T)c->phi_s);
+        else
+            lbm::k_color_step<T><<<nb, lbm::kCB, 0, c->stream>>>(R, (const T*)c->phi, c->L, c->d_prm, (T)c->sp,
+                                                                 (T)c->sm, (T)c->alpha, (T)c->beta, (T)c->phi_s);
         return cudaGetLastError();
     });
     COLOR_CUDA(c, e);

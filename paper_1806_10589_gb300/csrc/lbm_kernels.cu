@@ -120,7 +120,7 @@ __device__ __forceinline__ void st_stream(T* a, T v, uint64_t pol) {
 // Pull all 19 values of node i (padded voxel p): a pore source gives its own
 // value, a solid or outside source the node's opposite value (halfway
 // bounce-back; the z-outside ones are replaced by the closure).
-template <class S>
+template <class S, bool OFF32 = false>
 __device__ __forceinline__ void pull_step(typename S::M* d, const StepPtrs<typename S::T>& P,
                                           const DevLattice& L, uint32_t p, int i, uint64_t pol_f,
                                           uint64_t pol_idx, typename S::M r_own, typename S::M g) {
@@ -132,7 +132,12 @@ __device__ __forceinline__ void pull_step(typename S::M* d, const StepPtrs<typen
         } else {
             // padded voxel indices fit in 32 bits (checked at creation)
             const int id = ld_index(L.grid + (uint32_t)(p + (uint32_t)L.goff[Q]), pol_idx);
-            const typename S::T* a = id >= 0 ? P.in[Q] + id : P.in[opp(Q)] + i;
+            const typename S::T* a;
+            if constexpr (OFF32)  // row 0 plus one 32-bit element offset (rows are ns apart)
+                a = P.in[0] + (id >= 0 ? (uint32_t)Q * (uint32_t)L.ns + (uint32_t)id
+                                       : (uint32_t)opp(Q) * (uint32_t)L.ns + (uint32_t)i);
+            else
+                a = id >= 0 ? P.in[Q] + id : P.in[opp(Q)] + i;
             // a pulled value was written on plane z - xi_z (reference r_own - g xi_z)
             const M r = (cz(Q) != 0 && id >= 0) ? r_own - M(cz(Q)) * g : r_own;
             d[Q] = S::template dec<Q>(ld_stream(a, pol_f), r);
@@ -342,7 +347,9 @@ __device__ __forceinline__ double next_inlet_part_stored(const StepPtrs<typename
     });
 }
 
-template <class S>
+// OFF32: pulls addressed as row 0 plus a 32-bit element offset (buffers of
+// 19 ns < 2^32 elements), as in the gather-scatter AA step.
+template <class S, bool OFF32 = false>
 __global__ void __launch_bounds__(kBlock, step_min_blocks<S>())
 k_step(const StepPtrs<typename S::T> P, int slot, DevLattice L, typename S::M sp, typename S::M sm,
        BcState* bc, double* __restrict__ partials, unsigned* __restrict__ counter) {
@@ -367,7 +374,7 @@ k_step(const StepPtrs<typename S::T> P, int slot, DevLattice L, typename S::M sp
         const M r_own = own_ref<S>(bc, L, p), g = own_slope<S>(bc);
         const uint32_t seed = step_seed<S>(bc, slot);
         M d[19];
-        pull_step<S>(d, P, L, p, i, pol_f, pol_idx, r_own, g);
+        pull_step<S, OFF32>(d, P, L, p, i, pol_f, pol_idx, r_own, g);
         if (i < L.a_in) {
             // Section 2: after streaming, before collision.  u_z from Eq. (inlet)
             // with the density of Eq. (potential); then the Appendix B closure.
@@ -1209,8 +1216,13 @@ cudaError_t launch_step(int prec, const void* fin, void* fout, int slot, const D
             P.in[q] = (const T*)fin + (int64_t)q * L.ns;
             P.out[q] = (T*)fout + (int64_t)q * L.ns;
         }
-        k_step<S><<<blocks_for(L.n, kBlock), kBlock, 0, st>>>(P, slot, L, (M)r.sp, (M)r.sm, bc, partials,
-                                                               counter);
+        // GB300_LBM_STEP_ADDR64 forces the 64-bit form (tests)
+        if (19 * (uint64_t)L.ns <= 0xFFFFFFFFull && !std::getenv("GB300_LBM_STEP_ADDR64"))
+            k_step<S, true><<<blocks_for(L.n, kBlock), kBlock, 0, st>>>(P, slot, L, (M)r.sp, (M)r.sm, bc,
+                                                                         partials, counter);
+        else
+            k_step<S><<<blocks_for(L.n, kBlock), kBlock, 0, st>>>(P, slot, L, (M)r.sp, (M)r.sm, bc, partials,
+                                                                   counter);
         return cudaGetLastError();
     });
 }

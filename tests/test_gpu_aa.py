@@ -82,17 +82,19 @@ def test_aa_equals_two_buffer_kernel(torch_cuda, prec, chunks):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16dev", "bf16dev"])
-def test_aa_32bit_offsets_equal_64bit_addresses(torch_cuda, prec, monkeypatch):
-    """The gather-scatter launch addresses its neighbours as row 0 plus a 32-bit
-    element offset whenever the buffer has fewer than 2^32 elements; the 64-bit
-    form (two row pointers) serves larger lattices.  Both compute the same step,
-    so the states are bitwise equal (the 64-bit form is forced by the
-    GB300_LBM_AA_ADDR64 switch; graphs are captured per lattice, after it is set)."""
+@pytest.mark.parametrize("variant, switch", [(3, "GB300_LBM_AA_ADDR64"), (0, "GB300_LBM_STEP_ADDR64")])
+def test_32bit_offsets_equal_64bit_addresses(torch_cuda, prec, variant, switch, monkeypatch):
+    """The gather-scatter AA launch and the two-buffer step address their
+    neighbours as row 0 plus a 32-bit element offset whenever the buffer has
+    fewer than 2^32 elements; the 64-bit form (two row pointers) serves larger
+    lattices.  Both compute the same step, so the states are bitwise equal (the
+    64-bit form is forced by an environment switch; graphs are captured per
+    lattice, after it is set)."""
     m = random_mask(37, 29, 21, 0.3, 8)
     chunks = [1, 64, 3]
-    a = _run(m, prec, 3, chunks, torch_cuda)
-    monkeypatch.setenv("GB300_LBM_AA_ADDR64", "1")
-    b = _run(m, prec, 3, chunks, torch_cuda)
+    a = _run(m, prec, variant, chunks, torch_cuda)
+    monkeypatch.setenv(switch, "1")
+    b = _run(m, prec, variant, chunks, torch_cuda)
     np.testing.assert_array_equal(a[0], b[0])
     assert a[1] == b[1] and a[2] == b[2]
 

@@ -82,6 +82,30 @@ def test_colour_fp32_matches_oracle(torch_cuda):
     assert np.abs(B - ref.B).max() <= 20 * N * EPS32 * np.abs(ref.B).max()
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_colour_32bit_offsets_equal_64bit_addresses(torch_cuda, prec, monkeypatch):
+    """The colour step addresses gathered momentum values and pushed D3Q7 values
+    as row 0 plus a 32-bit element offset when the buffers have fewer than 2^32
+    elements, else by 64-bit row pointers; both forms give bitwise the same state
+    (the 64-bit form is forced by GB300_LBM_COLOR_ADDR64)."""
+    from paper_1806_10589_gb300 import ColorLattice
+
+    m = random_mask(9, 8, 12, 0.25, 43)
+    ref = _case(m, 70, -0.5)
+    out = []
+    for force in (False, True):
+        if force:
+            monkeypatch.setenv("GB300_LBM_COLOR_ADDR64", "1")
+        with ColorLattice(m, 0.8, 0.01, 0.9, -0.5, prec, stream=torch_cuda.cuda.current_stream()) as c:
+            c.set_flux_bc(0.004, 1.0)
+            c.set_state(ref.f.copy(), ref.A.copy(), ref.B.copy())
+            c.step(15)
+            out.append(c.state() + (c.get_flux(4),))
+    for x, y in zip(out[0][:3], out[1][:3]):
+        np.testing.assert_array_equal(x, y)
+    assert out[0][3] == out[1][3]
+
+
 def test_colour_single_phase_limit_equals_single_fluid(torch_cuda):
     from paper_1806_10589_gb300 import ColorLattice, Lattice
 
