@@ -90,7 +90,9 @@ int lbm_set_flux_bc(lbm_ctx* ctx, int face, double Q);
 int lbm_set_pressure_bc(lbm_ctx* ctx, int face, double rho);
 
 /* Use this CUDA stream (a cudaStream_t passed as void*, e.g. a PyTorch stream
- * handle) for all later device work of this context.  NULL = default stream. */
+ * handle) for all later device work of this context.  NULL = default stream.
+ * A variant-3 state left in the in-place layout is swapped back on the
+ * previous stream first. */
 int lbm_set_stream(lbm_ctx* ctx, void* cuda_stream);
 
 /* Select the step-kernel variant.  Every variant computes the same step:
@@ -101,10 +103,14 @@ int lbm_set_stream(lbm_ctx* ctx, void* cuda_stream);
  * one 256-node tile ahead; 2 = the same with 128-node tiles; 3 = AA pattern:
  * ONE distribution buffer updated in place (the second buffer is freed, so the
  * state needs half the memory), alternating a gather-scatter step and a
- * node-local step; every storage format.  Each
- * lbm_step call on variant 3 adds two in-place layout swaps (three for an odd
- * step count; 16-bit formats also at every reference-profile refresh), so that
- * between calls the state reads exactly as with the other variants.  Leaving variant 3 allocates the second buffer again
+ * node-local step; every storage format.  On
+ * variant 3 the first lbm_step call swaps the buffer into the in-place layout
+ * (one launch), and the buffer stays in that layout across lbm_step calls,
+ * which continue the alternation where the last call left it.  Any other call
+ * on the context swaps it back first, on the context's stream (one launch, two
+ * after an odd number of steps); 16-bit formats also swap back at every
+ * reference-profile refresh.  So every call that reads or writes the state
+ * sees it exactly as with the other variants.  Leaving variant 3 allocates the second buffer again
  * (LBM_ENOMEM if that fails; the context stays on variant 3).  Unknown
  * variants return LBM_EINVAL.  Synchronises. */
 int lbm_set_kernel(lbm_ctx* ctx, int variant);
@@ -113,7 +119,8 @@ int lbm_set_kernel(lbm_ctx* ctx, int variant);
  * follows Section 2's order: pull streaming with halfway bounce-back at solid
  * voxels, the inlet density reduction (Eq. potential), the pressure closures at
  * inlet and outlet (Appendix B), then collision (Appendix A) at every pore node.
- * Runs of 64 steps are replayed from captured CUDA graphs. */
+ * Runs of 64 steps are replayed from captured CUDA graphs.  On variant 3 the
+ * buffer is left in the AA pattern's in-place layout (see lbm_set_kernel). */
 int lbm_step(lbm_ctx* ctx, int n);
 
 /* Measured flux through a face: Q = sum of u_z over the face's pore nodes of the

@@ -45,6 +45,11 @@ struct lbm_ctx {
     void* f[2] = {nullptr, nullptr};
     int cur = 0;     // buffer of the state (pull variants) and parity of the inlet-density slot
     bool aa = false; // AA pattern: the state lives in f[0] alone, f[1] is released
+    // AA pattern: the buffer stays in the in-place layout between lbm_step calls
+    // (aa_resident); aa_phase = 0 when the next launch gathers and scatters, 1
+    // when it is node-local.  Every other call swaps it back first (aa_settle).
+    bool aa_resident = false;
+    int aa_phase = 0;
     uint32_t* d_vox = nullptr;
     int* d_grid = nullptr;
     lbm::BcState h_bc{};
@@ -58,7 +63,7 @@ struct lbm_ctx {
     double* d_u_ref = nullptr;  // velocity snapshot of the steady-state criterion (allocated on first use)
     cudaStream_t stream = nullptr;
     cudaStream_t cap_stream = nullptr;
-    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    cudaGraphExec_t graph[4] = {nullptr, nullptr, nullptr, nullptr};  // [cur + 2 aa_phase]
     int64_t steps = 0;
     int64_t since_reencode = 0;  // steps since the 16-bit reference profile was refreshed
     int ref_e = 0;               // profile slot the stored values are encoded with
@@ -91,12 +96,16 @@ int fail(lbm_ctx* c, int code, const char* fmt, ...) {
             return fail((ctx), LBM_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
     } while (0)
 
-int enter(lbm_ctx* c) {
+int aa_settle(lbm_ctx* c);
+
+// Every entry point but lbm_step: select the device and bring a resident AA
+// layout back to the pull layout the other calls read and write.
+int enter(lbm_ctx* c, bool settle = true) {
     if (!c) return LBM_EINVAL;
     if (c->status == LBM_ECUDA) return LBM_ECUDA;
     cudaError_t e = cudaSetDevice(c->device);
     if (e != cudaSuccess) return fail(c, LBM_ECUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
-    return LBM_OK;
+    return settle ? aa_settle(c) : LBM_OK;
 }
 
 // Buffer that holds the current state (pull layout in every variant).
@@ -118,12 +127,25 @@ int one_step(lbm_ctx* c, cudaStream_t st) {
     return LBM_OK;
 }
 
-// AA pattern: step number k of a call (k = 0 first) is odd-type (gather-scatter)
-// for even k and node-local for odd k; the call's layout swaps surround them.
-int aa_step(lbm_ctx* c, int64_t k, cudaStream_t st) {
-    LBM_CUDA(c, lbm::launch_aa_step(c->prec, c->f[0], (k & 1) == 0, c->cur, c->L, c->relax, c->d_bc,
+// AA pattern, in the in-place layout: a gather-scatter launch when aa_phase is 0,
+// a node-local one when it is 1; the two alternate across lbm_step calls.
+int aa_step(lbm_ctx* c, cudaStream_t st) {
+    LBM_CUDA(c, lbm::launch_aa_step(c->prec, c->f[0], c->aa_phase == 0, c->cur, c->L, c->relax, c->d_bc,
                                     c->d_red_partials, c->d_step_counter, st));
     c->cur ^= 1;
+    c->aa_phase ^= 1;
+    return LBM_OK;
+}
+
+// AA pattern: from the in-place layout back to the pull layout (an un-stream
+// swap after a gather-scatter launch, then the opposite-pair swap), on the
+// context's stream.  A no-op when the layout is not resident.
+int aa_settle(lbm_ctx* c) {
+    if (!c->aa_resident) return LBM_OK;
+    if (c->aa_phase) LBM_CUDA(c, lbm::launch_aa_unstream(c->prec, c->f[0], c->L, c->d_bc, c->stream));
+    LBM_CUDA(c, lbm::launch_aa_swap(c->prec, c->f[0], c->L, c->stream));
+    c->aa_resident = false;
+    c->aa_phase = 0;
     return LBM_OK;
 }
 
@@ -146,21 +168,26 @@ int maybe_reencode(lbm_ctx* c) {
     return prime_inlet(c);
 }
 
-int build_graph(lbm_ctx* c, int parity) {
-    const int saved = c->cur;
-    c->cur = parity;
+// Graph slot gi = cur + 2 aa_phase: kGraphSteps steps starting from that buffer
+// parity (and, on the AA pattern, that launch kind).
+int build_graph(lbm_ctx* c, int gi) {
+    static_assert(kGraphSteps % 2 == 0, "a graph must preserve the buffer parity and the AA phase");
+    const int saved = c->cur, saved_phase = c->aa_phase;
+    c->cur = gi & 1;
+    c->aa_phase = gi >> 1;
     cudaGraph_t g = nullptr;
     LBM_CUDA(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
     int rc = LBM_OK;
-    for (int k = 0; k < kGraphSteps && rc == LBM_OK; ++k) rc = c->aa ? aa_step(c, k, c->cap_stream) : one_step(c, c->cap_stream);
+    for (int k = 0; k < kGraphSteps && rc == LBM_OK; ++k) rc = c->aa ? aa_step(c, c->cap_stream) : one_step(c, c->cap_stream);
     cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
     c->cur = saved;
+    c->aa_phase = saved_phase;
     if (rc != LBM_OK) {
         if (g) cudaGraphDestroy(g);
         return rc;
     }
     if (e != cudaSuccess) return fail(c, LBM_ECUDA, "graph capture: %s", cudaGetErrorString(e));
-    e = cudaGraphInstantiate(&c->graph[parity], g, 0);
+    e = cudaGraphInstantiate(&c->graph[gi], g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return fail(c, LBM_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
     return LBM_OK;
@@ -413,28 +440,34 @@ int lbm_set_kernel(lbm_ctx* c, int variant) {
 }
 
 int lbm_step(lbm_ctx* c, int n) {
-    int rc = enter(c);
+    int rc = enter(c, false);
     if (rc) return rc;
     if (n < 0) return fail(c, LBM_EINVAL, "n must be >= 0");
     if (c->aa) {
-        // segments end where the 16-bit reference profile is refreshed, which
-        // works on the resting (pull) layout
+        // The buffer enters the in-place layout once and stays in it across
+        // calls; segments end where the 16-bit reference profile is refreshed,
+        // which works on the pull layout.
         int64_t done = 0;
         while (done < n) {
-            if ((rc = maybe_reencode(c))) return rc;
+            if (c->prec >= LBM_PREC_FP16DEV && c->since_reencode >= kReencodeInterval) {
+                if ((rc = aa_settle(c)) || (rc = maybe_reencode(c))) return rc;
+            }
             int64_t seg = n - done;
             if (c->prec >= LBM_PREC_FP16DEV) seg = std::min<int64_t>(seg, kReencodeInterval - c->since_reencode);
-            LBM_CUDA(c, lbm::launch_aa_swap(c->prec, c->f[0], c->L, c->stream));
+            if (!c->aa_resident) {
+                LBM_CUDA(c, lbm::launch_aa_swap(c->prec, c->f[0], c->L, c->stream));
+                c->aa_resident = true;
+                c->aa_phase = 0;
+            }
             int64_t k = 0;
             while (seg - k >= kGraphSteps) {
-                if (!c->graph[c->cur] && (rc = build_graph(c, c->cur))) return rc;
-                LBM_CUDA(c, cudaGraphLaunch(c->graph[c->cur], c->stream));
+                const int gi = c->cur + 2 * c->aa_phase;
+                if (!c->graph[gi] && (rc = build_graph(c, gi))) return rc;
+                LBM_CUDA(c, cudaGraphLaunch(c->graph[gi], c->stream));
                 k += kGraphSteps;
             }
             for (; k < seg; ++k)
-                if ((rc = aa_step(c, k, c->stream))) return rc;
-            if (seg & 1) LBM_CUDA(c, lbm::launch_aa_unstream(c->prec, c->f[0], c->L, c->d_bc, c->stream));
-            LBM_CUDA(c, lbm::launch_aa_swap(c->prec, c->f[0], c->L, c->stream));
+                if ((rc = aa_step(c, c->stream))) return rc;
             done += seg;
             c->since_reencode += seg;
         }

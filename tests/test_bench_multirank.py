@@ -72,3 +72,22 @@ def test_ensemble_steady_summary():
     assert out["steps_all_steady"] is None
     assert out["steps_median_member"] == (first_ok + 1) * every
     assert "0.1%" in out["criterion"]
+
+
+def test_timed_launch_count():
+    """The benchmark's count of library launches in the timed call.  FP32 on the
+    AA pattern: the warm-up call leaves the buffer in the in-place layout, so the
+    timed call is its K step launches; the two-buffer kernel is K launches too.
+    16-bit AA, warm-up 5 and 1100 timed steps: the refresh falls after 1019
+    timed steps, 1024 since the swap-in (an even count: no un-stream), so the
+    swap back, re-encode, inlet density and a new swap-in add 4 launches; the
+    two-buffer kernel adds the re-encode and the inlet density."""
+    import bench
+
+    assert bench.timed_launches(5, 20, 3, "fp32") == 20
+    assert bench.timed_launches(3, 10000, 3, "fp32") == 10000
+    assert bench.timed_launches(0, 20, 3, "fp32") == 21
+    assert bench.timed_launches(5, 200, 0, "fp32") == 200
+    assert bench.timed_launches(5, 1100, 3, "fp16dev") == 1100 + 4
+    assert bench.timed_launches(5, 1000, 3, "fp16dev") == 1000
+    assert bench.timed_launches(5, 2000, 0, "bf16dev") == 2000 + 2

@@ -12,6 +12,8 @@ buffer updated in place).
   allocates it again, mid-run, without changing the trajectory.
 * 16-bit deviation storage on the AA pattern: oracle bound and a crossing of
   the reference-profile refresh.
+* Calls: the buffer stays in the in-place layout between lbm_step calls, so a
+  run split into calls equals one call bit for bit; reads in between swap it back.
 """
 import numpy as np
 import pytest
@@ -124,6 +126,54 @@ def test_aa_switching_mid_run_releases_and_restores_memory(torch_cuda):
     assert free1 - free2 >= buf - (2 << 20), (free1, free2, buf)
     dev = np.abs(ref - O.W[:, None, None, None] * (m == 0)).max()
     assert np.abs(got - ref).max() <= 40 * EPS32 * dev
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16dev", "bf16dev"])
+@pytest.mark.parametrize("chunks,whole", [([5, 71], 76), ([1, 64, 2, 1], 68), ([700, 401], 1101)])
+def test_aa_calls_continue_in_place(torch_cuda, prec, chunks, whole):
+    """Between lbm_step calls the AA buffer stays in its in-place layout and the
+    next call continues the alternation of gather-scatter and node-local launches
+    (graphs for either starting launch), so splitting a run into calls gives
+    bitwise the state, fluxes and inlet density of one call, in every format
+    (the 16-bit reference refresh falls on the same step either way)."""
+    m = random_mask(13, 11, 10, 0.3, 3)
+    a, a_in, a_out = _run(m, prec, 3, chunks, torch_cuda, seed=9)
+    b, b_in, b_out = _run(m, prec, 3, [whole], torch_cuda, seed=9)
+    assert np.array_equal(a, b), np.abs(a - b).max()
+    assert a_in == b_in and a_out == b_out
+
+
+@pytest.mark.parametrize("steps", [7, 8])
+def test_aa_reads_between_calls(torch_cuda, steps):
+    """A read between calls swaps the buffer back (with the un-stream after an
+    odd step count) and the next call swaps it in again; the layout-changing
+    calls in between (monitors, flux, time_kernels) leave the trajectory equal to
+    the two-buffer kernel's to FP32 rounding, N eps max|d| after N steps, and the
+    FP64 run equal to the oracle."""
+    from paper_1806_10589_gb300 import Lattice
+
+    m = random_mask(37, 29, 21, 0.3, 8)
+    out = {}
+    for prec, v in (("fp32", 0), ("fp32", 3), ("fp64", 3)):
+        with Lattice(m, 0.8, "mrt", prec, stream=torch_cuda.cuda.current_stream()) as lat:
+            lat.set_kernel(v)
+            lat.set_flux_bc(0.002)
+            lat.set_distributions(_f0(m, 5))
+            lat.step(steps)
+            lat.monitors()
+            lat.step(steps)
+            lat.get_flux(4)
+            lat.time_kernels(3)
+            lat.step(steps + 1)
+            out[(prec, v)] = lat.distributions()
+    N = 3 * steps + 4
+    a, b = out[("fp32", 0)], out[("fp32", 3)]
+    dev = np.abs(a - O.W[:, None, None, None] * (m == 0)).max()
+    assert np.abs(a - b).max() <= N * EPS32 * dev
+    ref = O.D3Q19Oracle(m, 0.8, "mrt", Q=0.002)
+    ref.set_distributions(_f0(m, 5))
+    ref.step(N)
+    assert np.abs(out[("fp64", 3)] - ref.f).max() <= 1e-11 * np.abs(ref.f).max()
 
 
 @pytest.mark.parametrize("prec,bits", [("fp16dev", 11), ("bf16dev", 8)])
