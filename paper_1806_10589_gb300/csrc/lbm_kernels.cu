@@ -517,6 +517,16 @@ __device__ __forceinline__ uint64_t aa_index_policy() {
 #endif
 }
 
+// LBM_AA_SMEM_OFF: 1 = with ids staged in shared memory (LBM_AA16_IDS /
+// LBM_AA_IDS 2) and 32-bit offsets, the gather stores each direction's element
+// offset instead of its id.  The scatter destination of q is the gather source
+// of opp(q) -- F[q][x + xi_q] for a pore there, else the bounce-back slot
+// F[opp q][x], both read by the gather of opp(q) -- so the scatter reads its
+// offset as it is and needs no id test or offset arithmetic; 0 = ids staged.
+#ifndef LBM_AA_SMEM_OFF
+#define LBM_AA_SMEM_OFF 0
+#endif
+
 // OFF32 (gather-scatter launch, buffers of 19 ns < 2^32 elements): every
 // neighbour address is row 0 plus one 32-bit element offset, the source or
 // destination row chosen by a 32-bit select, instead of a select between two
@@ -530,6 +540,8 @@ k_step_aa(const AAPtrs<typename S::T> F, int slot, DevLattice L, typename S::M s
     __shared__ double sh[32];
     __shared__ bool last;
     constexpr int kIds = S::kRef ? LBM_AA16_IDS : LBM_AA_IDS;
+    // staged per direction: the gather's element offset (kOffs) or the pore id
+    constexpr bool kOffs = OFF32 && kIds == 2 && LBM_AA_SMEM_OFF;
     __shared__ int sid[(ODD && kIds == 2) ? 18 : 1][kBlock];
     const int64_t i64 = (int64_t)blockIdx.x * kBlock + threadIdx.x;
     const int i = (int)i64;
@@ -562,24 +574,30 @@ k_step_aa(const AAPtrs<typename S::T> F, int slot, DevLattice L, typename S::M s
             for_q(std::make_integer_sequence<int, 18>{}, [&](auto qc) {
                 constexpr int Q = decltype(qc)::value + 1;
                 nb[Q] = ld_aa_index(L.grid + (uint32_t)(p + (uint32_t)L.goff[Q]), pol_idx);
-                if constexpr (kIds == 2) sid[Q - 1][threadIdx.x] = nb[Q];
+                if constexpr (kIds == 2 && !kOffs) sid[Q - 1][threadIdx.x] = nb[Q];
                 if constexpr (S::kRef) {
                     // 16-bit (instruction-bound): one load and one decode, the
                     // source slot and its plane selected
                     const bool pore = nb[Q] >= 0;
                     const typename S::T* src;
-                    if constexpr (OFF32)  // one 32-bit element offset from row 0 (the rows are ns apart)
-                        src = F.row[0] + (pore ? (uint32_t)opp(Q) * (uint32_t)L.ns + (uint32_t)nb[Q]
-                                               : (uint32_t)Q * (uint32_t)L.ns + (uint32_t)i);
-                    else
+                    if constexpr (OFF32) {  // one 32-bit element offset from row 0 (the rows are ns apart)
+                        const uint32_t off = pore ? (uint32_t)opp(Q) * (uint32_t)L.ns + (uint32_t)nb[Q]
+                                                  : (uint32_t)Q * (uint32_t)L.ns + (uint32_t)i;
+                        if constexpr (kOffs) sid[Q - 1][threadIdx.x] = (int)off;
+                        src = F.row[0] + off;
+                    } else {
                         src = pore ? F.row[opp(Q)] + nb[Q] : F.row[Q] + i;
+                    }
                     d[Q] = S::template dec<Q>(*src, pore ? r_own - M(cz(Q)) * g : r_own);
                 } else {
-                    if constexpr (OFF32)
-                        d[Q] = F.row[0][nb[Q] >= 0 ? (uint32_t)opp(Q) * (uint32_t)L.ns + (uint32_t)nb[Q]
-                                                    : (uint32_t)Q * (uint32_t)L.ns + (uint32_t)i];
-                    else
+                    if constexpr (OFF32) {
+                        const uint32_t off = nb[Q] >= 0 ? (uint32_t)opp(Q) * (uint32_t)L.ns + (uint32_t)nb[Q]
+                                                        : (uint32_t)Q * (uint32_t)L.ns + (uint32_t)i;
+                        if constexpr (kOffs) sid[Q - 1][threadIdx.x] = (int)off;
+                        d[Q] = F.row[0][off];
+                    } else {
                         d[Q] = nb[Q] >= 0 ? F.row[opp(Q)][nb[Q]] : F.row[Q][i];
+                    }
                 }
             });
         } else {
@@ -612,7 +630,26 @@ k_step_aa(const AAPtrs<typename S::T> F, int slot, DevLattice L, typename S::M s
                 else if constexpr (kIds == 2) return sid[opp(Q) - 1][threadIdx.x];
                 else return nb[opp(Q)];
             };
-            if constexpr (S::kRef && !LBM_AA16_PAIR_SCATTER) {
+            if constexpr (kOffs) {
+                // the destination of Q is the gather source of opp(Q), its offset
+                // staged by this thread; a pore destination lies in row Q, a
+                // bounce-back one in row opp(Q)
+                for_q(std::make_integer_sequence<int, 18>{}, [&](auto qc) {
+                    constexpr int Q = decltype(qc)::value + 1;
+                    const uint32_t off = (uint32_t)sid[opp(Q) - 1][threadIdx.x];
+                    if constexpr (S::kRef) {
+                        M r = r_own;
+                        if constexpr (cz(Q) != 0) {
+                            const bool pore = (Q & 1) ? off < (uint32_t)(Q + 1) * (uint32_t)L.ns
+                                                      : off >= (uint32_t)Q * (uint32_t)L.ns;
+                            r = pore ? r_own + M(cz(Q)) * g : r_own;
+                        }
+                        F.row[0][off] = S::template enc_sr<Q>(d[Q], r, sr_key<S>(seed, i, Q));
+                    } else {
+                        F.row[0][off] = d[Q];
+                    }
+                });
+            } else if constexpr (S::kRef && !LBM_AA16_PAIR_SCATTER) {
                 for_q(std::make_integer_sequence<int, 18>{}, [&](auto qc) {
                     constexpr int Q = decltype(qc)::value + 1;
                     const int dst = dest(qc_t<Q>{});
