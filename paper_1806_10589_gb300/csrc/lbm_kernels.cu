@@ -434,10 +434,12 @@ k_step(const StepPtrs<typename S::T> P, int slot, DevLattice L, typename S::M sp
 // post-collision value does not depend on where it is stored.
 // Where the gather-scatter step keeps its 18 neighbour ids across the
 // collision (LBM_AA_IDS): 0 = registers (spills at the 64-register cap),
-// 1 = loads them again from the id grid, 2 = shared memory (18 KB per block).
-// Measured best: 1 for FP32 (and FP64), 2 for the 16-bit formats (LBM_AA16_IDS).
+// 1 = loads them again from the id grid, 2 = shared memory (18 KB per block;
+// with LBM_AA_SMEM_OFF the gather offsets instead of the ids).  Measured best:
+// 2 for every format (LBM_AA16_IDS for the 16-bit ones); with ids instead of
+// offsets staged, 1 and 2 were equal in FP32.
 #ifndef LBM_AA_IDS
-#define LBM_AA_IDS 1
+#define LBM_AA_IDS 2
 #endif
 #ifndef LBM_AA16_IDS
 #define LBM_AA16_IDS 2
@@ -523,8 +525,12 @@ __device__ __forceinline__ uint64_t aa_index_policy() {
 // of opp(q) -- F[q][x + xi_q] for a pore there, else the bounce-back slot
 // F[opp q][x], both read by the gather of opp(q) -- so the scatter reads its
 // offset as it is and needs no id test or offset arithmetic; 0 = ids staged.
+// Measured on the 256^3 pack (same-call A/B, bitwise equal states): the
+// gather-scatter launch 0.2006 -> 0.1825 ms (FP16-dev), 0.2024 -> 0.1840 ms
+// (BF16-dev), and with the FP32 ids staged as well (LBM_AA_IDS 2; staged ids
+// alone gave 0.2007 ms) 0.2013 -> 0.1972 ms.
 #ifndef LBM_AA_SMEM_OFF
-#define LBM_AA_SMEM_OFF 0
+#define LBM_AA_SMEM_OFF 1
 #endif
 
 // OFF32 (gather-scatter launch, buffers of 19 ns < 2^32 elements): every
