@@ -454,10 +454,13 @@ struct AAPtrs {
 };
 
 // Resident blocks per SM the two AA kernels are compiled for (register caps).
-// The FP32 gather-scatter step measured best at 4 (64 registers) with the L2
-// prefetch below, at 5 (48 registers, with spills) without it.
+// The FP32 gather-scatter step measured best at 5 (48 registers): with the
+// gather offsets staged in shared memory it compiles there without spills, and
+// its launch took 0.1897 ms against 0.1970 ms at 4 (64 registers).  (With the
+// ids reloaded for the scatter, 4 was best with the L2 prefetch, 5 with spills
+// without it.)
 #ifndef LBM_AA_MIN_BLOCKS
-#define LBM_AA_MIN_BLOCKS 4
+#define LBM_AA_MIN_BLOCKS 5
 #endif
 #ifndef LBM_AA_EVEN_MIN_BLOCKS
 #define LBM_AA_EVEN_MIN_BLOCKS 6
