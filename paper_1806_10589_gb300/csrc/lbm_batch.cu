@@ -364,14 +364,23 @@ __global__ void k_barrier_probe(GridBarrier* bar, unsigned expected, long long l
 // opposite pairs, alternates gather-scatter (odd) and node-local (even) steps,
 // and swaps back (after an odd count an un-stream swap comes first).  Ids are
 // global pore indices, so the scatter stays inside the member.  16-bit values
-// are encoded with the reference of the plane of the node that holds them; the
-// gather-scatter step loads its ids again for the scatter.
+// are encoded with the reference of the plane of the node that holds them.  In
+// the 32-bit offset form the gather-scatter step stages each direction's gather
+// offset in shared memory (LBM_BATCH_AA_STAGE): the scatter destination of q is
+// the slot the gather of opp(q) read, so the scatter needs neither the voxel
+// index nor the ids again; otherwise it loads them again for the scatter.
 // Row pointers of the store as kernel parameters (constant bank): no registers
 // spent on 19 row addresses.
 template <class T>
 struct Rows {
     T* row[19];
 };
+
+// Measured on the 64-member FP16-dev ensemble (same-call A/B, bitwise equal
+// states): AA configuration 1.157 -> 1.068 ms per step, AA-capped 1.223 -> 1.136.
+#ifndef LBM_BATCH_AA_STAGE
+#define LBM_BATCH_AA_STAGE 1
+#endif
 
 template <class S, bool ODD, int MINB, bool OFF32 = false>
 __global__ void __launch_bounds__(kTile, batch_min_blocks<S, MINB>())
@@ -380,6 +389,8 @@ k_batch_aa(const Rows<typename S::T> F, int slot, const uint32_t* __restrict__ v
            typename S::M sm, double* __restrict__ partials, unsigned* __restrict__ counters) {
     using M = typename S::M;
     __shared__ double sh[32];
+    constexpr bool kStage = ODD && OFF32 && LBM_BATCH_AA_STAGE;
+    __shared__ uint32_t soff[kStage ? 18 : 1][kStage ? kTile : 1];  // gather offset per direction and node
     if constexpr (ODD) batch_prefetch(F.row[0], F.row[1] - F.row[0], vox);  // rows are ns apart, as launched
     const int64_t tile = blockIdx.x;
     const int mi = tile_member[tile];
@@ -401,9 +412,9 @@ k_batch_aa(const Rows<typename S::T> F, int slot, const uint32_t* __restrict__ v
                 const int id = __ldg(grid + p + m.goff[Q]);
                 if constexpr (OFF32) {
                     const bool pore = id >= 0;
-                    d[Q] = S::template dec<Q>(F.row[0][pore ? (uint32_t)opp(Q) * ns32 + (uint32_t)id
-                                                            : (uint32_t)Q * ns32 + (uint32_t)i],
-                                              pore ? r_own - M(cz(Q)) * g : r_own);
+                    const uint32_t off = pore ? (uint32_t)opp(Q) * ns32 + (uint32_t)id : (uint32_t)Q * ns32 + (uint32_t)i;
+                    if constexpr (kStage) soff[Q - 1][threadIdx.x] = off;
+                    d[Q] = S::template dec<Q>(F.row[0][off], pore ? r_own - M(cz(Q)) * g : r_own);
                 } else {
                     d[Q] = id >= 0 ? S::template dec<Q>(F.row[opp(Q)][id], r_own - M(cz(Q)) * g)
                                    : S::template dec<Q>(F.row[Q][i], r_own);
@@ -431,7 +442,22 @@ k_batch_aa(const Rows<typename S::T> F, int slot, const uint32_t* __restrict__ v
         // addresses would keep 19 64-bit addresses live across the collision)
         int64_t j;
         asm volatile("mov.b64 %0, %1;" : "=l"(j) : "l"(i));
-        if constexpr (ODD) {
+        if constexpr (kStage) {
+            F.row[0][j] = S::template enc_sr<0>(d[0], r_own, sr_key<S>(seed, i, 0));
+            // the destination of Q is the gather source of opp(Q): row Q for a pore
+            // there, row opp(Q) (bounce-back) otherwise
+            const uint32_t ns32 = (uint32_t)(F.row[1] - F.row[0]);
+            for_q(std::make_integer_sequence<int, 18>{}, [&](auto qc) {
+                constexpr int Q = decltype(qc)::value + 1;
+                const uint32_t off = soff[opp(Q) - 1][threadIdx.x];
+                M r = r_own;
+                if constexpr (S::kRef && cz(Q) != 0) {
+                    const bool pore = (Q & 1) ? off < (uint32_t)(Q + 1) * ns32 : off >= (uint32_t)Q * ns32;
+                    r = pore ? r_own + M(cz(Q)) * g : r_own;
+                }
+                F.row[0][off] = S::template enc_sr<Q>(d[Q], r, sr_key<S>(seed, i, Q));
+            });
+        } else if constexpr (ODD) {
             const int64_t ps = __ldg(vox + j);
             F.row[0][j] = S::template enc_sr<0>(d[0], r_own, sr_key<S>(seed, i, 0));
             if constexpr (OFF32) {
