@@ -120,7 +120,16 @@ int lbm_set_kernel(lbm_ctx* ctx, int variant);
  * voxels, the inlet density reduction (Eq. potential), the pressure closures at
  * inlet and outlet (Appendix B), then collision (Appendix A) at every pore node.
  * Runs of 64 steps are replayed from captured CUDA graphs.  On variant 3 the
- * buffer is left in the AA pattern's in-place layout (see lbm_set_kernel). */
+ * buffer is left in the AA pattern's in-place layout (see lbm_set_kernel).
+ * Stream capture of the context's stream: runs of 64 steps launch the
+ * library's own graphs, which a capturing stream rejects (LBM_ECUDA).  The
+ * host-side buffer parity, layout and step count advance when a call is made,
+ * not when recorded work replays.  So on variant 3 a call made while the
+ * stream captures keeps the pull layout at its start and end, and a buffer left
+ * in the in-place layout by an earlier call makes it, and every other call that
+ * would swap the layout back inside the capture, return LBM_EINVAL instead of
+ * recording a swap; make any other call on the context (e.g. lbm_set_stream)
+ * before the capture begins. */
 int lbm_step(lbm_ctx* ctx, int n);
 
 /* Measured flux through a face: Q = sum of u_z over the face's pore nodes of the

@@ -98,6 +98,18 @@ int fail(lbm_ctx* c, int code, const char* fmt, ...) {
 
 int aa_settle(lbm_ctx* c);
 
+// True while the context's stream records a CUDA graph.  A failing query (the
+// legacy stream while another stream captures globally) counts as not
+// capturing; the launches that follow report that case themselves.
+bool stream_capturing(lbm_ctx* c) {
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(c->stream, &st) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return st != cudaStreamCaptureStatusNone;
+}
+
 // Every entry point but lbm_step: select the device and bring a resident AA
 // layout back to the pull layout the other calls read and write.
 int enter(lbm_ctx* c, bool settle = true) {
@@ -140,13 +152,25 @@ int aa_step(lbm_ctx* c, cudaStream_t st) {
 // AA pattern: from the in-place layout back to the pull layout (an un-stream
 // swap after a gather-scatter launch, then the opposite-pair swap), on the
 // context's stream.  A no-op when the layout is not resident.
-int aa_settle(lbm_ctx* c) {
+int aa_settle_launch(lbm_ctx* c) {
     if (!c->aa_resident) return LBM_OK;
     if (c->aa_phase) LBM_CUDA(c, lbm::launch_aa_unstream(c->prec, c->f[0], c->L, c->d_bc, c->stream));
     LBM_CUDA(c, lbm::launch_aa_swap(c->prec, c->f[0], c->L, c->stream));
     c->aa_resident = false;
     c->aa_phase = 0;
     return LBM_OK;
+}
+
+// Host state (buffer parity, layout) advances when a call is made, so a graph
+// recorded from the calls must start and end in the pull layout to be replayed.
+constexpr const char* kResidentInCapture =
+    "the AA-pattern buffer is in its in-place layout while the stream records a graph; "
+    "make any other call on the context (e.g. lbm_set_stream) before the capture begins";
+
+int aa_settle(lbm_ctx* c) {
+    if (!c->aa_resident) return LBM_OK;
+    if (stream_capturing(c)) return fail(c, LBM_EINVAL, "%s", kResidentInCapture);
+    return aa_settle_launch(c);
 }
 
 // Inlet density for the current buffer when the state or Q changed outside a
@@ -443,14 +467,18 @@ int lbm_step(lbm_ctx* c, int n) {
     int rc = enter(c, false);
     if (rc) return rc;
     if (n < 0) return fail(c, LBM_EINVAL, "n must be >= 0");
+    if (n == 0) return LBM_OK;
     if (c->aa) {
         // The buffer enters the in-place layout once and stays in it across
         // calls; segments end where the 16-bit reference profile is refreshed,
-        // which works on the pull layout.
+        // which works on the pull layout.  A call recorded into a graph starts
+        // and ends in the pull layout instead.
+        const bool capturing = stream_capturing(c);
+        if (capturing && c->aa_resident) return fail(c, LBM_EINVAL, "%s", kResidentInCapture);
         int64_t done = 0;
         while (done < n) {
             if (c->prec >= LBM_PREC_FP16DEV && c->since_reencode >= kReencodeInterval) {
-                if ((rc = aa_settle(c)) || (rc = maybe_reencode(c))) return rc;
+                if ((rc = aa_settle_launch(c)) || (rc = maybe_reencode(c))) return rc;
             }
             int64_t seg = n - done;
             if (c->prec >= LBM_PREC_FP16DEV) seg = std::min<int64_t>(seg, kReencodeInterval - c->since_reencode);
@@ -471,6 +499,7 @@ int lbm_step(lbm_ctx* c, int n) {
             done += seg;
             c->since_reencode += seg;
         }
+        if (capturing && (rc = aa_settle_launch(c))) return rc;
         c->steps += n;
         return LBM_OK;
     }

@@ -255,3 +255,4 @@ def test_aa_fp32_steady_duct_matches_poiseuille_series(torch_cuda):
     assert err < 5e-3, err
     assert abs(sim.sum() - Q) < 1e-3 * Q
     assert abs(q_out - Q) < 1e-3 * Q
+
